@@ -1,0 +1,124 @@
+"""ctypes front end of the natural-order C oracle (oracle/bm_oracle.c).
+
+ORACLE -- test infrastructure only (see oracle/__init__.py).
+
+Natural order = (dx^1, ..., dx^M, dx_0) with each tail dx^i = (dx_1, ..., dx_N)
+(Sec. III-B); this is Fig. 2(a)'s ordering, whose factor carries a dense root
+row. Every function takes and returns float64 NumPy arrays in the layouts of
+``bmgen``.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        lib.bmo_factor.restype = ctypes.c_long
+        lib.bmo_factor.argtypes = [ctypes.c_int] * 4 + [_dp] * 9 + [ctypes.c_int]
+        lib.bmo_solve.restype = None
+        lib.bmo_solve.argtypes = [ctypes.c_int] * 4 + [_dp] * 6 + [ctypes.c_int]
+        lib.bmo_residual.restype = None
+        lib.bmo_residual.argtypes = [ctypes.c_int] * 4 + [_dp] * 8 + [ctypes.c_int]
+        lib.bmo_tail_schur_first.restype = ctypes.c_long
+        lib.bmo_tail_schur_first.argtypes = [ctypes.c_int] * 3 + [_dp] * 3 + [ctypes.c_int]
+        lib.bmo_max_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a):
+    a = np.asarray(a.cpu().numpy() if hasattr(a, "cpu") else a, dtype=np.float64)
+    return np.ascontiguousarray(a)
+
+
+class NotSPD(RuntimeError):
+    pass
+
+
+def max_threads() -> int:
+    return int(_load().bmo_max_threads())
+
+
+def factor(D, E, C, R, nthreads: int = 0) -> dict:
+    """Natural-order block Cholesky. Returns Ld[S,N,nb,nb], Lsub[S,N-1,nb,nb],
+    Z[S,N,nr,nb] (dense root row of the factor), LR[nr,nr] = chol(R - sum U),
+    Rt = R - sum U and logdet(K) = 2 sum log diag(L)."""
+    D, E, C, R = _f64(D), _f64(E), _f64(C), _f64(R)
+    S, N, nb, _ = D.shape
+    nr = R.shape[0]
+    if nb > 256:
+        raise ValueError("oracle supports nb <= 256")
+    Ld = np.zeros((S, N, nb, nb))
+    Lsub = np.zeros((S, max(N - 1, 0), nb, nb))
+    Z = np.zeros((S, N, nr, nb))
+    LR = np.zeros((nr, nr))
+    Rt = np.zeros((nr, nr))
+    Ep = E if E.size else np.zeros(1)
+    Lsp = Lsub if Lsub.size else np.zeros(1)
+    rc = _load().bmo_factor(S, N, nb, nr, _p(D), _p(Ep), _p(C), _p(R), _p(Ld), _p(Lsp), _p(Z),
+                            _p(LR), _p(Rt), int(nthreads))
+    if rc != 0:
+        raise NotSPD("oracle: non-positive pivot (code %d)" % rc)
+    logdet = 2.0 * (np.log(np.diagonal(Ld, axis1=-2, axis2=-1)).sum() + np.log(np.diag(LR)).sum())
+    return {"Ld": Ld, "Lsub": Lsub, "Z": Z, "LR": LR, "Rt": Rt, "logdet": float(logdet),
+            "shape": (S, N, nb, nr)}
+
+
+def solve(fac: dict, r, nthreads: int = 0) -> np.ndarray:
+    S, N, nb, nr = fac["shape"]
+    r = _f64(r)
+    x = np.zeros_like(r)
+    Lsub = fac["Lsub"] if fac["Lsub"].size else np.zeros(1)
+    _load().bmo_solve(S, N, nb, nr, _p(fac["Ld"]), _p(Lsub), _p(fac["Z"]), _p(fac["LR"]),
+                      _p(r), _p(x), int(nthreads))
+    return x
+
+
+def residual(D, E, C, R, x, r, nthreads: int = 0) -> dict:
+    """rho = r - K x in FP64 and the normwise backward error
+    eta = ||rho||_inf / (||K||_inf ||x||_inf + ||r||_inf)."""
+    D, E, C, R, x, r = (_f64(a) for a in (D, E, C, R, x, r))
+    S, N, nb, _ = D.shape
+    nr = R.shape[0]
+    rho = np.zeros_like(r)
+    out = np.zeros(6)
+    Ep = E if E.size else np.zeros(1)
+    _load().bmo_residual(S, N, nb, nr, _p(D), _p(Ep), _p(C), _p(R), _p(x), _p(r), _p(rho), _p(out),
+                         int(nthreads))
+    eta = out[0] / (out[1] * out[2] + out[3])
+    return {"rho": rho, "eta": float(eta), "rel2": float(out[4] / out[5]), "K_inf": float(out[1])}
+
+
+def tail_schur_first(D, E, nthreads: int = 0) -> np.ndarray:
+    """Per tail, the Schur complement onto stage 1 of the tail matrix K_i
+    (eliminating stages N, ..., 2): S_1 = ((K_i^{-1})_{11})^{-1}."""
+    D, E = _f64(D), _f64(E)
+    S, N, nb, _ = D.shape
+    out = np.zeros((S, nb, nb))
+    Ep = E if E.size else np.zeros(1)
+    rc = _load().bmo_tail_schur_first(S, N, nb, _p(D), _p(Ep), _p(out), int(nthreads))
+    if rc != 0:
+        raise NotSPD("oracle: non-positive pivot (code %d)" % rc)
+    return out
+
+
+def solve_system(sysd: dict, nthreads: int = 0) -> dict:
+    """Factor + solve + residual of one generated system (dict from bmgen)."""
+    fac = factor(sysd["D"], sysd["E"], sysd["C"], sysd["R"], nthreads)
+    x = solve(fac, sysd["r"], nthreads)
+    res = residual(sysd["D"], sysd["E"], sysd["C"], sysd["R"], x, sysd["r"], nthreads)
+    return {"x": x, "fac": fac, "res": res}
