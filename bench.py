@@ -1,0 +1,380 @@
+"""Benchmark: factor + solve of one branch-MPC KKT system per step.
+
+Default workload: the medium FP64 system (S=64 scenarios, N=64 stages,
+nb=12, nr=4, barrier diagonals 10^U[-4,4]), factored (Alg. 1) and solved
+(Alg. 2) through the C ABI with the inputs resident in HBM. One step =
+bm_factor + bm_solve. L2 is flushed (a 256 MiB write) between timed steps,
+outside the timed events.
+
+Prints ONE JSON line (rank 0). value = whole-job GFLOP/s, counting the
+method's flops of one factor + solve per step (the same per-step count for
+every arm, so value is proportional to KKT systems per second).
+  --impl reference : the CPU oracle (natural-order FP64 block Cholesky) on
+                     the host cores, timed on the same workload.
+  --workload NAME  : another synthetic workload (see bmgen.WORKLOADS).
+  --precision fp32ir : the FP32-tail + FP64-refinement path.
+Multi-GPU (torchrun): every rank factors and solves its own replica (the
+scenarios of one system are not split across GPUs); weak scaling.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+DEFAULT_WORKLOAD = "medium-s64-n64-nb12"
+METRIC = "factor+solve µs and GFLOP/s per branch KKT; FP32+IR vs FP64 at rel. residual 1e-10"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp64_peak_gflops(sm_mhz=None):
+    """FP64 ALU peak of the GPU: 152 SMs x 2 FMA lanes per clock (one 32-lane
+    warp instruction per 64 cycles on each of the 4 SM sub-partitions,
+    measured) x 2 flop per FMA x the maximum SM clock."""
+    peaks, _ = _peaks()
+    mhz = sm_mhz or peaks.get("sm_max_mhz", 2070.0)
+    return 152 * 2 * 2 * mhz * 1e6 / 1e9
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2609_29977_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _profile_traffic(workload, precision):
+    """Per-launch DRAM traffic of the factor pipeline from the committed ncu
+    summary (profiles/factor_<precision>_<workload>.txt), if the kernels have
+    not changed since it was taken; else None."""
+    p = os.path.join(ROOT, "profiles", "factor_%s_%s.txt" % (precision, workload))
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    with open(p) as f:
+        for line in f:
+            if ":" in line and line.split(":", 1)[0].strip() in ("source_hash", "traffic_bytes_per_factor"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("source_hash") != _kernel_source_hash():
+        return None
+    try:
+        return float(vals["traffic_bytes_per_factor"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def time_oracle(sysd, budget_s, min_reps=3, nthreads=0):
+    """The oracle's factor + solve, repeated on the full system until the
+    budget is spent; returns (seconds per factor+solve, threads, reps)."""
+    from oracle import natural
+    threads = nthreads or natural.max_threads()
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        natural.solve_system(sysd, nthreads=threads)
+        reps += 1
+        el = time.perf_counter() - t0
+        if reps >= min_reps and el >= budget_s:
+            break
+    return el / reps, threads, reps
+
+
+def gpu_backward_error(g, x):
+    """eta = ||r - K x||_inf / (||K||_inf ||x||_inf + ||r||_inf), plain PyTorch FP64."""
+    import torch
+    D, E, C, R, r = g["D"], g["E"], g["C"], g["R"], g["r"]
+    S, N, nb, _ = D.shape
+    nr = R.shape[0]
+    n0 = S * N * nb
+    X = x[:n0].view(S, N, nb, 1)
+    x0 = x[n0:]
+    Dl = torch.tril(D)
+    Df = Dl + torch.tril(Dl, -1).transpose(-1, -2)
+    Kx = (Df @ X).squeeze(-1)
+    rows = Df.abs().sum(-1)
+    if N > 1:
+        Kx[:, 1:] += (E @ X[:, :-1]).squeeze(-1)
+        Kx[:, :-1] += (E.transpose(-1, -2) @ X[:, 1:]).squeeze(-1)
+        rows[:, 1:] += E.abs().sum(-1)
+        rows[:, :-1] += E.abs().sum(-2)
+    Kx[:, 0] += (C.transpose(-1, -2) @ x0.view(1, nr, 1)).squeeze(-1)
+    rows[:, 0] += C.abs().sum(-2)
+    Rl = torch.tril(R)
+    Rf = Rl + torch.tril(Rl, -1).T
+    k0 = Rf @ x0 + (C @ X[:, 0]).squeeze(-1).sum(0)
+    rows0 = Rf.abs().sum(-1) + C.abs().sum(-1).sum(0)
+    rho = torch.cat([(r[:n0] - Kx.reshape(-1)), r[n0:] - k0])
+    kinf = torch.maximum(rows.max(), rows0.max())
+    eta = rho.abs().max() / (kinf * x.abs().max() + r.abs().max())
+    return float(eta), float(rho.norm() / r.norm())
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    import bmgen
+    w = bmgen.WORKLOADS[args.workload]
+    sysd = bmgen.generate(w)
+    fl = bmgen.method_flops(w.S, w.N, w.nb, w.nr)
+    budget = args.ref_budget
+    for _ in range(args.warmup):
+        time_oracle(sysd, 0.0, min_reps=1)
+    per = []
+    threads = 0
+    for _ in range(args.steps):
+        sec, threads, reps = time_oracle(sysd, budget / max(1, args.steps), min_reps=1)
+        per.append(sec)
+    sec = statistics.mean(per)
+    value = fl["total"] / sec / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "S": w.S, "N": w.N, "nb": w.nb, "nr": w.nr, "precision": "fp64",
+                   "solver": "oracle: natural-order FP64 block Cholesky (C, OpenMP over tails)"},
+        "us_per_kkt": sec * 1e6,
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+                         "sample": "full workload, factor+solve repeated per step for ~%.1f s" %
+                                   (budget / max(1, args.steps))},
+        "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+
+    import bmgen
+    import paper_2609_29977_gb300 as bm
+
+    rank, world, local = _env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = bm.BM_PREC_FP64 if args.precision == "fp64" else bm.BM_PREC_FP32_IR
+    w = bmgen.WORKLOADS[args.workload]
+    sysd = bmgen.generate(w, instance=rank)
+    g = {k: v.to(dev) for k, v in sysd.items() if isinstance(v, torch.Tensor)}
+    fl = bmgen.method_flops(w.S, w.N, w.nb, w.nr)
+    solver = bm.BranchKKTSolver(w.S, w.N, w.nb, w.nr, precision=prec, max_refine=args.max_refine,
+                                tol=args.tol)
+    x = torch.empty_like(g["r"])
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        solver.factor(g["D"], g["E"], g["C"], g["R"])
+        solver.solve(g["r"], x)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    info = solver.query()
+    if info["status"] != 0:
+        raise RuntimeError("device status after warm-up: %s" % info)
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [t for t in vis.split(",") if t.strip()]
+    smi_index = ids[local] if local < len(ids) and ids[local].strip().isdigit() else str(local)
+    sampler = ClockSampler(smi_index)
+    sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        a, b, c = ev[i]
+        a.record(stream)
+        solver.factor(g["D"], g["E"], g["C"], g["R"])
+        b.record(stream)
+        solver.solve(g["r"], x)
+        c.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    fac_ms = [a.elapsed_time(b) for a, b, _ in ev]
+    sol_ms = [b.elapsed_time(c) for _, b, c in ev]
+    tot_ms = sum(f + s for f, s in zip(fac_ms, sol_ms))
+    info = solver.query()
+    if dist:
+        t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    ms_per_step = tot_ms / args.steps
+    value = world * fl["total"] * args.steps / (tot_ms * 1e-3) / 1e9
+
+    # end to end through the public host-buffer entry point (pinned memory)
+    pin = {k: sysd[k].contiguous().pin_memory() for k in ("D", "E", "C", "R", "r")}
+    xh = torch.empty_like(pin["r"]).pin_memory()
+    for _ in range(2):
+        solver.factor_solve_host(pin["D"], pin["E"], pin["C"], pin["R"], pin["r"], xh)
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, code = solver.factor_solve_host(pin["D"], pin["E"], pin["C"], pin["R"], pin["r"], xh)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        if code != 0:
+            raise RuntimeError("host entry status %d" % code)
+    e2e_step = statistics.mean(e2e_ms)
+    if dist:
+        t = torch.tensor([e2e_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_step = float(t.item())
+    h2d = sum(pin[k].numel() * 8 for k in ("D", "E", "C", "R", "r"))
+    d2h = xh.numel() * 8
+
+    eta, rel2 = gpu_backward_error(g, x)
+    Lc = (w.N - 1).bit_length() if w.N > 1 else 0
+    launches_per_step = (Lc + 2) + (2 * Lc + 3)
+    fmean = statistics.mean(fac_ms)
+    peak_alu = fp64_peak_gflops()
+    achieved = fl["factor"] / (fmean * 1e-3) / 1e9
+    traffic = _profile_traffic(w.name, args.precision)
+    line = {
+        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic (seeded MPC-shaped generator; the paper's quadrotor data are not available)",
+        "config": {"workload": w.name, "S": w.S, "N": w.N, "nb": w.nb, "nr": w.nr,
+                   "precision": args.precision, "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "factor_us": fmean * 1e3, "solve_us": statistics.mean(sol_ms) * 1e3,
+        "us_per_kkt": ms_per_step * 1e3, "backward_error": eta, "rel_residual": rel2,
+        "device_status": info["name"],
+        "flops_per_kkt": {"method": fl["total"], "natural_order_factor": bmgen.natural_flops(w.S, w.N, w.nb, w.nr)},
+        "roofline": {"kernel": "factor pipeline (k_factor_level x %d + k_factor_x1 + k_factor_root, one graph)" % Lc,
+                     "bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "GFLOP/s",
+                     "frac": achieved / peak_alu, "traffic": traffic,
+                     "peak_source": "FP64 ALU derived: 152 SMs x 2 FMA/clk x 2 flop x %.0f MHz" %
+                                    _peaks()[0].get("sm_max_mhz", 2070.0)},
+        "e2e": {"value": world * fl["total"] / (e2e_step * 1e-3) / 1e9, "unit": "GFLOP/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "wall_s_timed": wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sec, threads, reps = time_oracle(sysd, args.ref_budget)
+        line["cpu_baseline"] = {"value": fl["total"] / sec / 1e9, "unit": "GFLOP/s", "cores": threads,
+                                "kind": "oracle",
+                                "sample": "full workload factor+solve x%d (%.1f s)" % (reps, sec * reps)}
+    solver.close()
+    if dist:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32ir"])
+    ap.add_argument("--max-refine", type=int, default=10)
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--ref-budget", type=float, default=10.0, help="seconds of oracle work")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

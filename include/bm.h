@@ -1,0 +1,179 @@
+/*
+ * bm.h -- C ABI of the GB300 branch-MPC direct solver.
+ *
+ * The solver factors and solves the SPD root-coupled system K dx = r of
+ * Sec. III-B (Eq. root_coupled_matrix): S scenario tails K_i, each
+ * block-tridiagonal over N stages with nb x nb blocks
+ * (Eq. tail_block_tridiagonal), coupled to one shared root block R (nr x nr)
+ * through a single block C_{i,1} on the first stage of every tail.
+ *
+ * The factorization is the two-level parallel Cholesky of Alg. 1 under the
+ * tail permutation Pi_i = blkdiag(Gamma_{N-1}, I) Omega_i of Sec. IV-A, and
+ * the solve is the two-level parallel forward/backward substitution of
+ * Alg. 2. Everything runs in CUDA kernels on the device; there is no CPU
+ * fallback.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All matrix/vector pointers are DEVICE pointers unless the name says
+ *   host, row-major, contiguous, float64, 16-byte aligned (cudaMalloc and
+ *   torch allocations satisfy this).
+ * - D[S][N][nb][nb]: stage blocks D_{i,k}; only the lower triangle is read.
+ * - E[S][N-1][nb][nb]: E[s][k] is the paper's E_{s,k+1}, the block at
+ *   (stage k+2, stage k+1) in 1-based stages (below the diagonal). For N = 1
+ *   the pointer may be NULL.
+ * - C[S][nr][nb]: the coupling blocks C_{i,1}; R[nr][nr]: the root block
+ *   (lower triangle read).
+ * - r, x[S*N*nb + nr]: natural order (dx^1, ..., dx^S, dx_0), each tail
+ *   dx^i = (dx^i_1, ..., dx^i_N) (Sec. III-B).
+ * - "stream" is a cudaStream_t passed as void*; NULL means the legacy
+ *   default stream. Every call that launches work is asynchronous with
+ *   respect to the host and ordered on that stream. Calls on one handle must
+ *   be ordered (one stream, or external synchronization): the handle's
+ *   workspaces are shared by its calls.
+ * - Argument errors are returned synchronously. Errors found on the device
+ *   (a non-positive pivot, refinement that did not converge) are recorded in
+ *   a sticky status word of the handle, reset by every bm_factor, and
+ *   returned by bm_query.
+ */
+#ifndef BM_H
+#define BM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BM_VERSION 1
+
+typedef struct bm_handle_s *bm_handle;
+
+typedef enum {
+  BM_OK = 0,
+  BM_ERR_INVALID_ARG = 1,   /* bad size, NULL pointer, misaligned pointer */
+  BM_ERR_NOT_SPD = 2,       /* a pivot was not positive and finite */
+  BM_ERR_OOM = 3,           /* device allocation failed in bm_analyze */
+  BM_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+  BM_ERR_NOT_CONVERGED = 5, /* mixed precision: refinement missed tol */
+  BM_ERR_TIMEOUT = 6,       /* a bounded device wait gave up */
+  BM_ERR_NOT_FACTORED = 7   /* bm_solve before any bm_factor */
+} bm_status;
+
+typedef enum {
+  BM_PREC_FP64 = 0,    /* factor and solve in FP64 */
+  BM_PREC_FP32_IR = 1  /* FP32 tails, FP64 root and FP64 refinement */
+} bm_precision;
+
+/* bm_desc.flags */
+#define BM_FLAG_NO_GRAPH 1u /* launch kernels directly instead of replaying captured CUDA graphs */
+
+typedef struct {
+  int S, N, nb, nr;   /* scenarios (the paper's M), horizon, stage block, root block */
+  int precision;      /* bm_precision */
+  int max_refine;     /* BM_PREC_FP32_IR: maximum refinement steps (<= 0: 10) */
+  double tol;         /* BM_PREC_FP32_IR: target normwise backward error (<= 0: 1e-10) */
+  unsigned flags;     /* BM_FLAG_* */
+} bm_desc;
+
+typedef struct {
+  int status;          /* sticky bm_status of the last bm_factor / bm_solve */
+  int fail_scenario;   /* BM_ERR_NOT_SPD: 0-based scenario, -1 for the root */
+  int fail_stage;      /* BM_ERR_NOT_SPD: 1-based stage k of that tail, 0 for the root */
+  int iters;           /* BM_PREC_FP32_IR: refinement steps of the last solve */
+  double backward_error; /* BM_PREC_FP32_IR: eta of the last solve; FP64: -1 */
+} bm_info;
+
+/* Library version (BM_VERSION). */
+int bm_version(void);
+
+/* Static string for a status code. */
+const char *bm_status_string(bm_status s);
+
+/*
+ * Device bytes that bm_analyze allocates for desc (factors and workspaces),
+ * or 0 for an invalid desc. The one-time analysis phase of Sec. V (fixed
+ * sparsity: persistent workspaces planned once).
+ */
+size_t bm_workspace_bytes(const bm_desc *desc);
+
+/*
+ * One-time analysis (Sec. V): validates desc (S, N, nb, nr >= 1; nb, nr <= 64;
+ * S <= 65535), plans the odd-even levels of Gamma_{N-1} (Sec. II), and
+ * allocates the handle's device memory on the current device. Kernels are
+ * captured into CUDA graphs lazily by the first bm_factor / bm_solve with
+ * a given set of pointers. On success *out owns all of it until bm_destroy.
+ * Errors: BM_ERR_INVALID_ARG, BM_ERR_OOM, BM_ERR_CUDA.
+ */
+bm_status bm_analyze(const bm_desc *desc, void *stream, bm_handle *out);
+
+/*
+ * Numeric factorization, Alg. 1 (steps 1-5): per tail the Cholesky factor
+ * L_i of Pi_i K_i Pi_i^T (horizon-parallel, Sec. IV-B), the coupling solve
+ * F_{i,1} = C_{i,1} L_{i,1}^{-T} (Theorem 1), the local Schur update
+ * U_i = F_{i,1} F_{i,1}^T, the root reduction R~ = R - sum_i U_i (FP64,
+ * fixed summation order) and L_R = chol(R~). Reads D, E, C, R (device);
+ * the handle owns the factor. Asynchronous. In BM_PREC_FP32_IR mode D, E,
+ * C, R must stay valid and unchanged until the next bm_factor or
+ * bm_destroy (the refinement residual reads them).
+ * Device-side failures (non-positive pivot) go to the sticky status.
+ */
+bm_status bm_factor(bm_handle h, const double *D, const double *E, const double *C,
+                    const double *R, void *stream);
+
+/*
+ * Triangular solves, Alg. 2: tail forward substitution (Pi_i r^i, L_i^{-1}),
+ * root reduction r~_0 = r_0 - sum_i F_{i,1} dy^i_1, root forward/backward
+ * substitution with L_R, root propagation dy^i_1 -= F_{i,1}^T dx_0, tail
+ * backward substitution and the inverse permutation. r and x are device
+ * vectors of length S*N*nb + nr in natural order; x must not alias r.
+ * BM_PREC_FP32_IR: iterative refinement on K with an FP64 residual until
+ * the backward error is <= tol or max_refine steps (status
+ * BM_ERR_NOT_CONVERGED then). Asynchronous.
+ * Errors: BM_ERR_INVALID_ARG, BM_ERR_NOT_FACTORED, BM_ERR_CUDA.
+ */
+bm_status bm_solve(bm_handle h, const double *r, double *x, void *stream);
+
+/*
+ * Synchronizes stream, then reports the sticky device status of the last
+ * bm_factor / bm_solve in *info (may be NULL) and returns it.
+ */
+bm_status bm_query(bm_handle h, void *stream, bm_info *info);
+
+/*
+ * Copies the factor of the last bm_factor into caller device buffers
+ * (each may be NULL to skip). Layout, by natural 1-based stage k of tail s
+ * (index [s][k-1]), with chain position p = N+1-k and level l = ctz(p) of
+ * Gamma_{N-1} for k >= 2:
+ *   Ld[S][N][nb][nb]: diagonal block L_pp of L_i (lower; k = 1: L_{i,1});
+ *   Ll[S][N][nb][nb]: the block of L_i in row p - 2^l, column p (zero if
+ *                     p <= 2^l, and for k = 1);
+ *   Lr[S][N][nb][nb]: the block in row p + 2^l (or row x_1 when
+ *                     p + 2^l > N-1), column p (zero for k = 1);
+ *   F[S][nr][nb]: F_{i,1};  LR[nr][nr]: L_R (lower).
+ * In BM_PREC_FP32_IR mode the FP32 tail factor is widened to FP64.
+ * Asynchronous on stream.
+ */
+bm_status bm_export_factor(bm_handle h, double *Ld, double *Ll, double *Lr, double *F,
+                           double *LR, void *stream);
+
+/*
+ * End-to-end convenience for callers whose data live in HOST memory:
+ * copies hD, hE, hC, hR, hr to device buffers owned by the handle
+ * (allocated on first use), runs bm_factor and bm_solve, copies x back to
+ * hx, and synchronizes stream before returning (hx is valid on return).
+ * Pinned (page-locked) host buffers give asynchronous copies.
+ * Returns the sticky device status like bm_query.
+ */
+bm_status bm_factor_solve_host(bm_handle h, const double *hD, const double *hE,
+                               const double *hC, const double *hR, const double *hr,
+                               double *hx, void *stream);
+
+/* Frees everything the handle owns (synchronizes its internal stream). */
+void bm_destroy(bm_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BM_H */

@@ -1,0 +1,220 @@
+"""ctypes binding of libbm.so (include/bm.h): argument marshalling only.
+
+Every function named ``bm_*`` here calls the C entry point of the same name.
+Tensors are torch tensors (device tensors for bm_factor / bm_solve, host
+tensors for bm_factor_solve_host); streams default to torch's current CUDA
+stream. There is no fallback: if the library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(HERE, "libbm.so")
+
+BM_PREC_FP64 = 0
+BM_PREC_FP32_IR = 1
+BM_FLAG_NO_GRAPH = 1
+
+BM_OK = 0
+STATUS_NAMES = {0: "BM_OK", 1: "BM_ERR_INVALID_ARG", 2: "BM_ERR_NOT_SPD", 3: "BM_ERR_OOM",
+                4: "BM_ERR_CUDA", 5: "BM_ERR_NOT_CONVERGED", 6: "BM_ERR_TIMEOUT",
+                7: "BM_ERR_NOT_FACTORED"}
+
+EXPORTED_SYMBOLS = ("bm_version", "bm_status_string", "bm_workspace_bytes", "bm_analyze", "bm_factor",
+                    "bm_solve", "bm_query", "bm_export_factor", "bm_factor_solve_host", "bm_destroy")
+
+
+class bm_desc(ctypes.Structure):
+    _fields_ = [("S", ctypes.c_int), ("N", ctypes.c_int), ("nb", ctypes.c_int), ("nr", ctypes.c_int),
+                ("precision", ctypes.c_int), ("max_refine", ctypes.c_int), ("tol", ctypes.c_double),
+                ("flags", ctypes.c_uint)]
+
+
+class bm_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("fail_scenario", ctypes.c_int), ("fail_stage", ctypes.c_int),
+                ("iters", ctypes.c_int), ("backward_error", ctypes.c_double)]
+
+
+class BMError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = int(code)
+        super().__init__("%s: %s (%s)" % (what, STATUS_NAMES.get(self.code, self.code),
+                                          bm_status_string(self.code)))
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError("libbm.so is not built (expected at %s); run __graft_entry__.build()" % _LIB_PATH)
+    lib = ctypes.CDLL(_LIB_PATH)
+    vp, dp, sz = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t
+    lib.bm_version.restype = ctypes.c_int
+    lib.bm_version.argtypes = []
+    lib.bm_status_string.restype = ctypes.c_char_p
+    lib.bm_status_string.argtypes = [ctypes.c_int]
+    lib.bm_workspace_bytes.restype = sz
+    lib.bm_workspace_bytes.argtypes = [ctypes.POINTER(bm_desc)]
+    lib.bm_analyze.restype = ctypes.c_int
+    lib.bm_analyze.argtypes = [ctypes.POINTER(bm_desc), vp, ctypes.POINTER(vp)]
+    lib.bm_factor.restype = ctypes.c_int
+    lib.bm_factor.argtypes = [vp, dp, dp, dp, dp, vp]
+    lib.bm_solve.restype = ctypes.c_int
+    lib.bm_solve.argtypes = [vp, dp, dp, vp]
+    lib.bm_query.restype = ctypes.c_int
+    lib.bm_query.argtypes = [vp, vp, ctypes.POINTER(bm_info)]
+    lib.bm_export_factor.restype = ctypes.c_int
+    lib.bm_export_factor.argtypes = [vp, dp, dp, dp, dp, dp, vp]
+    lib.bm_factor_solve_host.restype = ctypes.c_int
+    lib.bm_factor_solve_host.argtypes = [vp, dp, dp, dp, dp, dp, dp, vp]
+    lib.bm_destroy.restype = None
+    lib.bm_destroy.argtypes = [vp]
+    _lib = lib
+    return lib
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(t, name, device=True):
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch tensor" % name)
+    if t.dtype != torch.float64:
+        raise TypeError("%s must be float64" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if device != t.is_cuda:
+        raise ValueError("%s must be a %s tensor" % (name, "CUDA" if device else "host"))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(code, what):
+    if code != BM_OK:
+        raise BMError(code, what)
+
+
+def bm_version() -> int:
+    return int(_load().bm_version())
+
+
+def bm_status_string(code: int) -> str:
+    return _load().bm_status_string(int(code)).decode()
+
+
+def make_desc(S, N, nb, nr, precision=BM_PREC_FP64, max_refine=10, tol=1e-10, flags=0) -> bm_desc:
+    return bm_desc(int(S), int(N), int(nb), int(nr), int(precision), int(max_refine), float(tol), int(flags))
+
+
+def bm_workspace_bytes(desc: bm_desc) -> int:
+    return int(_load().bm_workspace_bytes(ctypes.byref(desc)))
+
+
+def bm_analyze(desc: bm_desc, stream=None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(_load().bm_analyze(ctypes.byref(desc), _stream(stream), ctypes.byref(h)), "bm_analyze")
+    return h
+
+
+def bm_factor(h, D, E, C, R, stream=None) -> None:
+    _check(_load().bm_factor(h, _ptr(D, "D"), _ptr(E, "E") if E is not None and E.numel() else None,
+                             _ptr(C, "C"), _ptr(R, "R"), _stream(stream)), "bm_factor")
+
+
+def bm_solve(h, r, x, stream=None) -> None:
+    _check(_load().bm_solve(h, _ptr(r, "r"), _ptr(x, "x"), _stream(stream)), "bm_solve")
+
+
+def bm_query(h, stream=None) -> dict:
+    info = bm_info()
+    code = _load().bm_query(h, _stream(stream), ctypes.byref(info))
+    return {"status": int(code), "name": STATUS_NAMES.get(int(code), str(code)),
+            "fail_scenario": info.fail_scenario, "fail_stage": info.fail_stage, "iters": info.iters,
+            "backward_error": info.backward_error}
+
+
+def bm_export_factor(h, Ld=None, Ll=None, Lr=None, F=None, LR=None, stream=None) -> None:
+    _check(_load().bm_export_factor(h, _ptr(Ld, "Ld"), _ptr(Ll, "Ll"), _ptr(Lr, "Lr"), _ptr(F, "F"),
+                                    _ptr(LR, "LR"), _stream(stream)), "bm_export_factor")
+
+
+def bm_factor_solve_host(h, D, E, C, R, r, x, stream=None) -> int:
+    """Host tensors in, host x out; returns the device status code."""
+    return int(_load().bm_factor_solve_host(
+        h, _ptr(D, "D", False), _ptr(E, "E", False) if E is not None and E.numel() else None,
+        _ptr(C, "C", False), _ptr(R, "R", False), _ptr(r, "r", False), _ptr(x, "x", False), _stream(stream)))
+
+
+def bm_destroy(h) -> None:
+    if h:
+        _load().bm_destroy(h)
+
+
+class BranchKKTSolver:
+    """Owns one bm_handle: analyze once, then factor / solve many times."""
+
+    def __init__(self, S, N, nb, nr, precision=BM_PREC_FP64, max_refine=10, tol=1e-10, flags=0, stream=None):
+        self.desc = make_desc(S, N, nb, nr, precision, max_refine, tol, flags)
+        self.shape = (S, N, nb, nr)
+        self.n = S * N * nb + nr
+        self.h = bm_analyze(self.desc, stream)
+
+    def factor(self, D, E, C, R, stream=None):
+        bm_factor(self.h, D, E, C, R, stream)
+        return self
+
+    def solve(self, r, x=None, stream=None):
+        import torch
+        if x is None:
+            x = torch.empty_like(r)
+        bm_solve(self.h, r, x, stream)
+        return x
+
+    def query(self, stream=None) -> dict:
+        return bm_query(self.h, stream)
+
+    def export_factor(self, stream=None) -> dict:
+        import torch
+        S, N, nb, nr = self.shape
+        dev = torch.device("cuda", torch.cuda.current_device())
+        out = {k: torch.empty((S, N, nb, nb), dtype=torch.float64, device=dev) for k in ("Ld", "Ll", "Lr")}
+        out["F"] = torch.empty((S, nr, nb), dtype=torch.float64, device=dev)
+        out["LR"] = torch.empty((nr, nr), dtype=torch.float64, device=dev)
+        bm_export_factor(self.h, out["Ld"], out["Ll"], out["Lr"], out["F"], out["LR"], stream)
+        return out
+
+    def factor_solve_host(self, D, E, C, R, r, x=None, stream=None):
+        import torch
+        if x is None:
+            x = torch.empty_like(r)
+        code = bm_factor_solve_host(self.h, D, E, C, R, r, x, stream)
+        return x, code
+
+    def close(self):
+        if self.h:
+            bm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,357 @@
+// C ABI of the library (include/bm.h): the one-time analysis that plans and
+// allocates (Sec. V), factor/solve entry points that replay CUDA graphs
+// captured per set of pointers (Sec. V: factor and solve pipelines are
+// captured separately), status handling and the host-buffer convenience
+// entry.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <new>
+
+#include "bm_internal.cuh"
+
+namespace bm {
+size_t f64_factor_smem(int nb, int nr);
+cudaError_t f64_prepare(int nb, int nr);
+void f64_launch_factor(const F64View &v, cudaStream_t st);
+void f64_launch_solve(const F64View &v, const double *r, double *x, double *r0t, cudaStream_t st);
+
+// mixed precision path (bm_mixed.cu)
+struct MixedState;
+size_t mixed_bytes(int S, int N, int nb, int nr);
+cudaError_t mixed_prepare(int nb, int nr);
+MixedState *mixed_create(int S, int N, int nb, int nr, void *base, size_t bytes, Status *status,
+                         unsigned *tickets);
+void mixed_destroy(MixedState *m);
+void mixed_launch_factor(MixedState *m, const double *D, const double *E, const double *C,
+                         const double *R, cudaStream_t st);
+void mixed_launch_solve(MixedState *m, const double *r, double *x, int max_refine, double tol,
+                        cudaStream_t st);
+void mixed_launch_export(MixedState *m, double *Ld, double *Ll, double *Lr, double *F, double *LR,
+                         cudaStream_t st);
+}  // namespace bm
+
+using namespace bm;
+
+struct GraphSlot {
+  cudaGraphExec_t exec = nullptr;
+  const void *key[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+
+struct bm_handle_s {
+  bm_desc desc;
+  int Lc = 0;
+  int device = 0;
+  void *pool = nullptr;
+  size_t pool_bytes = 0;
+  F64View v{};           // FP64 buffers (unused pointers null in mixed mode)
+  double *r0t = nullptr; // [nr] root right-hand side scratch
+  Status *status = nullptr;
+  unsigned *tickets = nullptr;
+  MixedState *mixed = nullptr;
+  cudaStream_t cap = nullptr;
+  GraphSlot gfac, gsol;
+  bool factored = false;
+  // host-entry staging (allocated on first use)
+  double *sD = nullptr, *sE = nullptr, *sC = nullptr, *sR = nullptr, *sr = nullptr, *sx = nullptr;
+};
+
+static bool valid_desc(const bm_desc *d) {
+  if (!d) return false;
+  if (d->S < 1 || d->N < 1 || d->nb < 1 || d->nr < 1) return false;
+  if (d->nb > 64 || d->nr > 64 || d->S > 65535) return false;
+  if (d->N > (1 << 24)) return false;
+  if (d->precision != BM_PREC_FP64 && d->precision != BM_PREC_FP32_IR) return false;
+  return true;
+}
+
+static size_t f64_bytes(int S, int N, int nb, int nr) {
+  const size_t SN = (size_t)S * N, b2 = (size_t)nb * nb;
+  size_t t = 0;
+  t += align_up(SN * b2 * sizeof(double), 256) * 5;          // Ld Ll Lr Dt W
+  t += align_up((size_t)S * nr * nb * sizeof(double), 256);  // F
+  t += align_up((size_t)S * nr * nr * sizeof(double), 256);  // U
+  t += align_up((size_t)nr * nr * sizeof(double), 256) * 2;  // LR Rt
+  t += align_up(SN * nb * sizeof(double), 256) * 3;          // invd y zt
+  t += align_up((size_t)S * nr * sizeof(double), 256);       // tb
+  t += align_up((size_t)nr * sizeof(double), 256);           // r0t
+  return t;
+}
+
+static const size_t kHeader = 512;   // status + tickets
+
+extern "C" int bm_version(void) { return BM_VERSION; }
+
+extern "C" const char *bm_status_string(bm_status s) {
+  switch (s) {
+    case BM_OK: return "ok";
+    case BM_ERR_INVALID_ARG: return "invalid argument";
+    case BM_ERR_NOT_SPD: return "matrix is not symmetric positive definite (non-positive pivot)";
+    case BM_ERR_OOM: return "device allocation failed";
+    case BM_ERR_CUDA: return "CUDA runtime error";
+    case BM_ERR_NOT_CONVERGED: return "iterative refinement did not reach the tolerance";
+    case BM_ERR_TIMEOUT: return "bounded device wait timed out";
+    case BM_ERR_NOT_FACTORED: return "solve called before factor";
+  }
+  return "unknown status";
+}
+
+extern "C" size_t bm_workspace_bytes(const bm_desc *d) {
+  if (!valid_desc(d)) return 0;
+  size_t t = kHeader;
+  if (d->precision == BM_PREC_FP64)
+    t += f64_bytes(d->S, d->N, d->nb, d->nr);
+  else
+    t += mixed_bytes(d->S, d->N, d->nb, d->nr);
+  return t;
+}
+
+extern "C" bm_status bm_analyze(const bm_desc *desc, void *stream, bm_handle *out) {
+  (void)stream;
+  if (!out) return BM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!valid_desc(desc)) return BM_ERR_INVALID_ARG;
+  bm_handle h = new (std::nothrow) bm_handle_s();
+  if (!h) return BM_ERR_OOM;
+  h->desc = *desc;
+  if (h->desc.max_refine <= 0) h->desc.max_refine = 10;
+  if (!(h->desc.tol > 0.0)) h->desc.tol = 1e-10;
+  const int S = desc->S, N = desc->N, nb = desc->nb, nr = desc->nr;
+  h->Lc = chain_levels(N);
+  cudaGetDevice(&h->device);
+  h->pool_bytes = bm_workspace_bytes(desc);
+  if (cudaMalloc(&h->pool, h->pool_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return BM_ERR_OOM;
+  }
+  if (cudaMemset(h->pool, 0, kHeader) != cudaSuccess) goto cuda_fail;
+  h->status = (Status *)h->pool;
+  h->tickets = (unsigned *)((char *)h->pool + 256);
+  if (desc->precision == BM_PREC_FP64) {
+    char *p = (char *)h->pool + kHeader;
+    const size_t SN = (size_t)S * N, b2 = (size_t)nb * nb;
+    auto take = [&](size_t bytes) {
+      double *q = (double *)p;
+      p += align_up(bytes, 256);
+      return q;
+    };
+    F64View &v = h->v;
+    v.S = S; v.N = N; v.nb = nb; v.nr = nr; v.Lc = h->Lc;
+    v.Ld = take(SN * b2 * 8); v.Ll = take(SN * b2 * 8); v.Lr = take(SN * b2 * 8);
+    v.Dt = take(SN * b2 * 8); v.W = take(SN * b2 * 8);
+    v.F = take((size_t)S * nr * nb * 8); v.U = take((size_t)S * nr * nr * 8);
+    v.LR = take((size_t)nr * nr * 8); v.Rt = take((size_t)nr * nr * 8);
+    v.invd = take(SN * nb * 8); v.y = take(SN * nb * 8); v.zt = take(SN * nb * 8);
+    v.tb = take((size_t)S * nr * 8);
+    h->r0t = take((size_t)nr * 8);
+    v.tickets = h->tickets;
+    v.status = h->status;
+    if (f64_prepare(nb, nr) != cudaSuccess) goto cuda_fail;
+  } else {
+    if (mixed_prepare(nb, nr) != cudaSuccess) goto cuda_fail;
+    h->mixed = mixed_create(S, N, nb, nr, (char *)h->pool + kHeader, h->pool_bytes - kHeader, h->status,
+                            h->tickets);
+    if (!h->mixed) goto cuda_fail;
+  }
+  if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) goto cuda_fail;
+  if (cudaDeviceSynchronize() != cudaSuccess) goto cuda_fail;
+  *out = h;
+  return BM_OK;
+cuda_fail:
+  cudaGetLastError();
+  if (h->mixed) mixed_destroy(h->mixed);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  cudaFree(h->pool);
+  delete h;
+  return BM_ERR_CUDA;
+}
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+static bool key_match(const GraphSlot &g, const void *const *k, int n) {
+  if (!g.exec) return false;
+  for (int i = 0; i < n; ++i)
+    if (g.key[i] != k[i]) return false;
+  return true;
+}
+
+// Runs body(stream) either directly or through the graph cached in slot
+// (re-captured on the handle's private stream when the pointers change).
+template <typename Body>
+static bm_status run(bm_handle h, GraphSlot &slot, const void *const *key, int nkey, cudaStream_t st,
+                     Body body) {
+  if (h->desc.flags & BM_FLAG_NO_GRAPH) {
+    body(st);
+    return cudaGetLastError() == cudaSuccess ? BM_OK : BM_ERR_CUDA;
+  }
+  if (!key_match(slot, key, nkey)) {
+    if (slot.exec) {
+      cudaGraphExecDestroy(slot.exec);
+      slot.exec = nullptr;
+    }
+    if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return BM_ERR_CUDA;
+    body(h->cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+    if (e != cudaSuccess || !g) {
+      cudaGetLastError();
+      return BM_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&slot.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      slot.exec = nullptr;
+      return BM_ERR_CUDA;
+    }
+    for (int i = 0; i < nkey; ++i) slot.key[i] = key[i];
+  }
+  return cudaGraphLaunch(slot.exec, st) == cudaSuccess ? BM_OK : BM_ERR_CUDA;
+}
+
+extern "C" bm_status bm_factor(bm_handle h, const double *D, const double *E, const double *C,
+                               const double *R, void *stream) {
+  if (!h || !D || !C || !R || (h->desc.N > 1 && !E)) return BM_ERR_INVALID_ARG;
+  if (!aligned16(D) || !aligned16(C) || !aligned16(R) || (E && !aligned16(E))) return BM_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const void *key[4] = {D, E, C, R};
+  bm_status s;
+  if (h->mixed) {
+    MixedState *m = h->mixed;
+    Status *status = h->status;
+    s = run(h, h->gfac, key, 4, st, [&](cudaStream_t cs) {
+      cudaMemsetAsync(status, 0, sizeof(Status), cs);
+      mixed_launch_factor(m, D, E, C, R, cs);
+    });
+  } else {
+    F64View v = h->v;
+    v.D = D; v.E = E; v.C = C; v.R = R;
+    s = run(h, h->gfac, key, 4, st, [&](cudaStream_t cs) {
+      cudaMemsetAsync(v.status, 0, sizeof(Status), cs);
+      f64_launch_factor(v, cs);
+    });
+    h->v.D = D; h->v.E = E; h->v.C = C; h->v.R = R;
+  }
+  if (s == BM_OK) h->factored = true;
+  return s;
+}
+
+extern "C" bm_status bm_solve(bm_handle h, const double *r, double *x, void *stream) {
+  if (!h || !r || !x || (const void *)r == (const void *)x) return BM_ERR_INVALID_ARG;
+  if (!aligned16(r) || !aligned16(x)) return BM_ERR_INVALID_ARG;
+  if (!h->factored) return BM_ERR_NOT_FACTORED;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (h->mixed) {
+    MixedState *m = h->mixed;
+    const int mr = h->desc.max_refine;
+    const double tol = h->desc.tol;
+    // the refinement residual reads the factor's inputs: key on them as well
+    const void *key[6] = {r, x, h->gfac.key[0], h->gfac.key[1], h->gfac.key[2], h->gfac.key[3]};
+    return run(h, h->gsol, key, 6, st, [&](cudaStream_t cs) { mixed_launch_solve(m, r, x, mr, tol, cs); });
+  }
+  F64View v = h->v;
+  double *r0t = h->r0t;
+  const void *key[2] = {r, x};
+  return run(h, h->gsol, key, 2, st, [&](cudaStream_t cs) { f64_launch_solve(v, r, x, r0t, cs); });
+}
+
+extern "C" bm_status bm_query(bm_handle h, void *stream, bm_info *info) {
+  if (!h) return BM_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+    cudaGetLastError();
+    return BM_ERR_CUDA;
+  }
+  Status st;
+  if (cudaMemcpy(&st, h->status, sizeof(Status), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return BM_ERR_CUDA;
+  }
+  if (info) {
+    info->status = st.code;
+    info->fail_scenario = st.code == BM_ERR_NOT_SPD ? st.scenario : 0;
+    info->fail_stage = st.code == BM_ERR_NOT_SPD ? st.stage : 0;
+    info->iters = h->mixed ? st.iters : 0;
+    info->backward_error = h->mixed ? st.eta : -1.0;
+  }
+  return (bm_status)st.code;
+}
+
+extern "C" bm_status bm_export_factor(bm_handle h, double *Ld, double *Ll, double *Lr, double *F,
+                                      double *LR, void *stream) {
+  if (!h) return BM_ERR_INVALID_ARG;
+  if (!h->factored) return BM_ERR_NOT_FACTORED;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (h->mixed) {
+    mixed_launch_export(h->mixed, Ld, Ll, Lr, F, LR, st);
+    return cudaGetLastError() == cudaSuccess ? BM_OK : BM_ERR_CUDA;
+  }
+  const F64View &v = h->v;
+  const size_t bb = (size_t)v.S * v.N * v.nb * v.nb * sizeof(double);
+  cudaError_t e = cudaSuccess;
+  if (Ld && e == cudaSuccess) e = cudaMemcpyAsync(Ld, v.Ld, bb, cudaMemcpyDeviceToDevice, st);
+  if (Ll && e == cudaSuccess) e = cudaMemcpyAsync(Ll, v.Ll, bb, cudaMemcpyDeviceToDevice, st);
+  if (Lr && e == cudaSuccess) e = cudaMemcpyAsync(Lr, v.Lr, bb, cudaMemcpyDeviceToDevice, st);
+  if (F && e == cudaSuccess)
+    e = cudaMemcpyAsync(F, v.F, (size_t)v.S * v.nr * v.nb * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  if (LR && e == cudaSuccess)
+    e = cudaMemcpyAsync(LR, v.LR, (size_t)v.nr * v.nr * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  return e == cudaSuccess ? BM_OK : BM_ERR_CUDA;
+}
+
+extern "C" bm_status bm_factor_solve_host(bm_handle h, const double *hD, const double *hE, const double *hC,
+                                          const double *hR, const double *hr, double *hx, void *stream) {
+  if (!h || !hD || !hC || !hR || !hr || !hx || (h->desc.N > 1 && !hE)) return BM_ERR_INVALID_ARG;
+  const int S = h->desc.S, N = h->desc.N, nb = h->desc.nb, nr = h->desc.nr;
+  const size_t nD = (size_t)S * N * nb * nb, nE = (size_t)S * (N - 1) * nb * nb;
+  const size_t nC = (size_t)S * nr * nb, nR = (size_t)nr * nr, n = (size_t)S * N * nb + nr;
+  if (!h->sD) {
+    void *p = nullptr;
+    const size_t bytes = align_up(nD * 8, 256) + align_up((nE ? nE : 1) * 8, 256) + align_up(nC * 8, 256) +
+                         align_up(nR * 8, 256) + 2 * align_up(n * 8, 256);
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return BM_ERR_OOM;
+    }
+    char *c = (char *)p;
+    h->sD = (double *)c; c += align_up(nD * 8, 256);
+    h->sE = (double *)c; c += align_up((nE ? nE : 1) * 8, 256);
+    h->sC = (double *)c; c += align_up(nC * 8, 256);
+    h->sR = (double *)c; c += align_up(nR * 8, 256);
+    h->sr = (double *)c; c += align_up(n * 8, 256);
+    h->sx = (double *)c;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(h->sD, hD, nD * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && nE) e = cudaMemcpyAsync(h->sE, hE, nE * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->sC, hC, nC * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->sR, hR, nR * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->sr, hr, n * 8, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return BM_ERR_CUDA;
+  }
+  bm_status s = bm_factor(h, h->sD, nE ? h->sE : nullptr, h->sC, h->sR, stream);
+  if (s != BM_OK) return s;
+  s = bm_solve(h, h->sr, h->sx, stream);
+  if (s != BM_OK) return s;
+  if (cudaMemcpyAsync(hx, h->sx, n * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+    cudaGetLastError();
+    return BM_ERR_CUDA;
+  }
+  return bm_query(h, stream, nullptr);
+}
+
+extern "C" void bm_destroy(bm_handle h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  if (h->gfac.exec) cudaGraphExecDestroy(h->gfac.exec);
+  if (h->gsol.exec) cudaGraphExecDestroy(h->gsol.exec);
+  if (h->mixed) mixed_destroy(h->mixed);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->sD) cudaFree(h->sD);
+  cudaFree(h->pool);
+  cudaGetLastError();
+  delete h;
+}

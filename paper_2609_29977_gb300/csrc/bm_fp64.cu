@@ -1,0 +1,516 @@
+// FP64 kernels of the two-level factorization (Alg. 1) and triangular
+// solves (Alg. 2).
+//
+// Schedule: one launch per odd-even level of Gamma_{N-1} (Sec. II), one CTA
+// per (tail, chain position) task of that level, so scenario-level and
+// horizon-level parallelism (Sec. IV, SLP and HLP) both map onto the grid.
+// Launch l does, for every position q still in the chain:
+//   * the Schur update collected from the level l-1 eliminations next to q
+//     (D~_q -= L_{q,p} L_{q,p}^T for the eliminated neighbours p), and
+//   * if q belongs to level l: L_qq = chol(D~_q), the coupling blocks
+//     L_{b,q} = M_{b,q} L_qq^{-T}, L_{a,q} = M_{a,q} L_qq^{-T} to its right
+//     and left neighbours b, a, and the fill coupling between them,
+//     M_{b,a} = -L_{b,q} L_{a,q}^T, which becomes a's right coupling.
+// Positions eliminated by one launch are never neighbours, every remaining
+// position gathers its own update, and every fill block has a single writer,
+// so no launch has a write race and no atomics are needed. x_1 (kept last by
+// Pi_i, Sec. IV-A) is factored by its own launch, which also forms the
+// coupling solve F_{i,1} = C_{i,1} L_{i,1}^{-T} (Theorem 1) and
+// U_i = F_{i,1} F_{i,1}^T. The root launch sums R - sum_i U_i in a fixed
+// order and the last CTA to finish factors it (Alg. 1, steps 4-5).
+//
+// GB300 notes: the FP64 pipe retires one warp instruction per 64 cycles per
+// SM sub-partition whatever the number of active lanes, so every loop below
+// hands out whole output elements across all threads of the CTA (each
+// thread's dot product is one dependent FMA chain), and the only
+// single-lane FP64 work is the pivot reciprocal square root.
+#include <math.h>
+
+#include "bm_internal.cuh"
+
+namespace bm {
+namespace {
+
+__device__ __forceinline__ void cta_copy(double *__restrict__ dst, const double *__restrict__ src, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+// dst (n x n) := src^T
+__device__ __forceinline__ void cta_copy_t(double *__restrict__ dst, const double *__restrict__ src, int n) {
+  const int n2 = n * n;
+  for (int e = threadIdx.x; e < n2; e += blockDim.x) {
+    const int i = e / n, j = e - i * n;
+    dst[j * n + i] = src[e];
+  }
+}
+__device__ __forceinline__ void cta_zero(double *dst, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = 0.0;
+}
+// global (n x n) := lower triangle of s, zeros above
+__device__ __forceinline__ void cta_store_lower(double *__restrict__ g, const double *__restrict__ s, int n) {
+  const int n2 = n * n;
+  for (int e = threadIdx.x; e < n2; e += blockDim.x) {
+    const int i = e / n, j = e - i * n;
+    g[e] = (j <= i) ? s[e] : 0.0;
+  }
+}
+
+// Lower-triangle element e -> (i, j) with j <= i.
+__device__ __forceinline__ void tri_ij(int e, int &i, int &j) {
+  int t = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+  while ((t + 1) * (t + 2) / 2 <= e) ++t;
+  while (t * (t + 1) / 2 > e) --t;
+  i = t;
+  j = e - t * (t + 1) / 2;
+}
+
+// lower(sD) -= X X^T + Y Y^T (n x n blocks, row-major; X or Y may be null).
+__device__ void cta_syrk_sub(double *sD, const double *X, const double *Y, int n) {
+  const int ne = n * (n + 1) / 2;
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+    int i, j;
+    tri_ij(e, i, j);
+    double acc = sD[i * n + j];
+    if (X)
+      for (int k = 0; k < n; ++k) acc = fma(-X[i * n + k], X[j * n + k], acc);
+    if (Y)
+      for (int k = 0; k < n; ++k) acc = fma(-Y[i * n + k], Y[j * n + k], acc);
+    sD[i * n + j] = acc;
+  }
+}
+
+// In-place lower Cholesky of the n x n block sA (lower triangle read);
+// sInv[j] = 1 / L_jj. A pivot that is not positive and finite is replaced by
+// 1 (so the launch finishes without NaNs) and the first such column + 1 is
+// returned; 0 on success.
+__device__ int cta_chol(double *sA, double *sInv, int n, int *sflag) {
+  if (threadIdx.x == 0) *sflag = 0;
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      double d = sA[j * n + j];
+      if (!(d > 0.0) || !(d < INFINITY)) {
+        if (*sflag == 0) *sflag = j + 1;
+        d = 1.0;
+      }
+      const double r = rsqrt(d);
+      sA[j * n + j] = d * r;
+      sInv[j] = r;
+    }
+    __syncthreads();
+    const double r = sInv[j];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) sA[i * n + j] *= r;
+    __syncthreads();
+    const int m = n - j - 1, ne = m * (m + 1) / 2;
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+      int a, b;
+      tri_ij(e, a, b);
+      const int i = j + 1 + a, k = j + 1 + b;
+      sA[i * n + k] = fma(-sA[i * n + j], sA[k * n + j], sA[i * n + k]);
+    }
+    __syncthreads();
+  }
+  return *sflag;
+}
+
+// X (m x n, row stride n) := X L^{-T}, L lower n x n with inverse diagonal inv.
+__device__ void cta_trsm_lt(double *X, int m, const double *L, const double *inv, int n) {
+  for (int j = 0; j < n; ++j) {
+    const double r = inv[j];
+    for (int row = threadIdx.x; row < m; row += blockDim.x) X[row * n + j] *= r;
+    __syncthreads();
+    const int cols = n - j - 1, ne = m * cols;
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+      const int row = e / cols, k = j + 1 + (e - row * cols);
+      X[row * n + k] = fma(-X[row * n + j], L[k * n + j], X[row * n + k]);
+    }
+    __syncthreads();
+  }
+}
+
+// Fixed-order CTA sum of one value per thread (blockDim.x a power of two).
+__device__ double cta_sum(double v, double *red) {
+  red[threadIdx.x] = v;
+  for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
+    __syncthreads();
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+  }
+  __syncthreads();
+  const double t = red[0];
+  __syncthreads();
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// Factorization
+// ---------------------------------------------------------------------------
+
+__global__ void k_factor_level(F64View v, int lvl) {
+  extern __shared__ double sm[];
+  __shared__ int sflag;
+  const int nb = v.nb, nb2 = nb * nb, N = v.N, s = blockIdx.y;
+  const int mb = nb > v.nr ? nb : v.nr;
+  double *sD = sm;
+  double *sB = sD + mb * mb;   // right coupling, then L_{b,q}
+  double *sA = sB + nb2;       // left coupling, then L_{a,q} (stacked under sB)
+  double *sInv = sB + (2 * nb2 > v.nr * nb ? 2 * nb2 : v.nr * nb);
+  const int q = level_task_pos(N, lvl, blockIdx.x);
+  const bool elim = (q < N) && (ctz32(q) == lvl);
+  const size_t sb = (size_t)s * N;
+
+  cta_copy(sD, (lvl <= 1 ? v.D : v.Dt) + (sb + (N - q)) * nb2, nb2);
+  if (lvl >= 1) {
+    const int h = 1 << (lvl - 1);
+    int pl = 0, pr = 0;
+    if (q < N) {
+      pl = q - h;
+      if (q + h <= N - 1) pr = q + h;
+    } else {
+      const int m = ((N - 1) >> (lvl - 1)) << (lvl - 1);
+      if (ctz32(m) == lvl - 1) pl = m;
+    }
+    if (pl) cta_copy(sB, v.Lr + (sb + (N - pl)) * nb2, nb2);
+    if (pr) cta_copy(sA, v.Ll + (sb + (N - pr)) * nb2, nb2);
+    __syncthreads();
+    cta_syrk_sub(sD, pl ? sB : nullptr, pr ? sA : nullptr, nb);
+  }
+  if (!elim) {
+    __syncthreads();
+    cta_copy(v.Dt + (sb + (N - q)) * nb2, sD, nb2);
+    return;
+  }
+  __syncthreads();
+  if (cta_chol(sD, sInv, nb, &sflag) && threadIdx.x == 0) report_not_spd(v.status, s, N + 1 - q);
+  cta_store_lower(v.Ld + (sb + (N - q)) * nb2, sD, nb);
+  const int h = 1 << lvl;
+  const bool hasA = q > h;
+  const int a = q - h;
+  // M_{b,q}: the original coupling A_{q+1,q} = E^T at level 0 (and for the
+  // last chain position, whose right neighbour is always x_1), else the fill
+  // block left by the previous level.
+  if (lvl == 0 || q == N - 1)
+    cta_copy_t(sB, v.E + ((size_t)s * (N - 1) + (N - q - 1)) * nb2, nb);
+  else
+    cta_copy(sB, v.W + (sb + (N - q)) * nb2, nb2);
+  if (hasA) {
+    if (lvl == 0)
+      cta_copy(sA, v.E + ((size_t)s * (N - 1) + (N - q)) * nb2, nb2);   // A_{q-1,q}
+    else
+      cta_copy_t(sA, v.W + (sb + (N - a)) * nb2, nb);                  // M_{q,a}^T
+  }
+  __syncthreads();
+  cta_trsm_lt(sB, hasA ? 2 * nb : nb, sD, sInv, nb);
+  cta_copy(v.Lr + (sb + (N - q)) * nb2, sB, nb2);
+  if (hasA) {
+    cta_copy(v.Ll + (sb + (N - q)) * nb2, sA, nb2);
+    double *Wa = v.W + (sb + (N - a)) * nb2;   // becomes M_{b,a}
+    for (int e = threadIdx.x; e < nb2; e += blockDim.x) {
+      const int i = e / nb, j = e - i * nb;
+      double acc = 0.0;
+      for (int k = 0; k < nb; ++k) acc = fma(-sB[i * nb + k], sA[j * nb + k], acc);
+      Wa[e] = acc;
+    }
+  } else {
+    cta_zero(v.Ll + (sb + (N - q)) * nb2, nb2);
+  }
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) v.invd[(sb + (N - q)) * nb + i] = sInv[i];
+}
+
+// x_1: last Schur update, L_{i,1}, F_{i,1} = C_{i,1} L_{i,1}^{-T}, U_i.
+__global__ void k_factor_x1(F64View v) {
+  extern __shared__ double sm[];
+  __shared__ int sflag;
+  const int nb = v.nb, nb2 = nb * nb, N = v.N, nr = v.nr, s = blockIdx.x, Lc = v.Lc;
+  const int mb = nb > nr ? nb : nr;
+  double *sD = sm, *sB = sD + mb * mb;
+  double *sInv = sB + (2 * nb2 > nr * nb ? 2 * nb2 : nr * nb);
+  const size_t sb = (size_t)s * N;
+  cta_copy(sD, (Lc <= 1 ? v.D : v.Dt) + sb * nb2, nb2);
+  if (Lc >= 1) {
+    const int m = 1 << (Lc - 1);
+    cta_copy(sB, v.Lr + (sb + (N - m)) * nb2, nb2);
+    __syncthreads();
+    cta_syrk_sub(sD, sB, nullptr, nb);
+  }
+  __syncthreads();
+  if (cta_chol(sD, sInv, nb, &sflag) && threadIdx.x == 0) report_not_spd(v.status, s, 1);
+  cta_store_lower(v.Ld + sb * nb2, sD, nb);
+  cta_zero(v.Ll + sb * nb2, nb2);
+  cta_zero(v.Lr + sb * nb2, nb2);
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) v.invd[sb * nb + i] = sInv[i];
+  cta_copy(sB, v.C + (size_t)s * nr * nb, nr * nb);
+  __syncthreads();
+  cta_trsm_lt(sB, nr, sD, sInv, nb);
+  cta_copy(v.F + (size_t)s * nr * nb, sB, nr * nb);
+  double *Us = v.U + (size_t)s * nr * nr;
+  for (int e = threadIdx.x; e < nr * nr; e += blockDim.x) {
+    const int i = e / nr, j = e - i * nr;
+    double acc = 0.0;
+    for (int k = 0; k < nb; ++k) acc = fma(sB[i * nb + k], sB[j * nb + k], acc);
+    Us[e] = acc;
+  }
+}
+
+// Root: R~ = R - sum_i U_i (one CTA per lower-triangle element, fixed
+// summation order), then L_R = chol(R~) by the last CTA to finish.
+__global__ void k_factor_root(F64View v) {
+  extern __shared__ double sm[];
+  __shared__ double red[256];
+  __shared__ int sflag, last;
+  const int nr = v.nr, S = v.S;
+  int i, j;
+  tri_ij(blockIdx.x, i, j);
+  double acc = 0.0;
+  for (int s = threadIdx.x; s < S; s += blockDim.x) acc += v.U[(size_t)s * nr * nr + i * nr + j];
+  const double tot = cta_sum(acc, red);
+  if (threadIdx.x == 0) {
+    const double val = v.R[i * nr + j] - tot;
+    v.Rt[i * nr + j] = val;
+    v.Rt[j * nr + i] = val;
+    __threadfence();
+    last = (atomicAdd(&v.tickets[0], 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double *sR = sm, *sInv = sm + nr * nr;
+  for (int e = threadIdx.x; e < nr * nr; e += blockDim.x) sR[e] = __ldcg(v.Rt + e);
+  __syncthreads();
+  if (cta_chol(sR, sInv, nr, &sflag) && threadIdx.x == 0) report_not_spd(v.status, -1, 0);
+  cta_store_lower(v.LR, sR, nr);
+  if (threadIdx.x == 0) v.tickets[0] = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// Solve (uses the inverse diagonals the factor kept in invd[S][N][nb])
+// ---------------------------------------------------------------------------
+
+// y := L^{-1} z in place (L lower n x n in shared memory, inverse diagonal inv).
+__device__ void cta_trsv_l(double *z, const double *L, const double *inv, int n) {
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) z[j] *= inv[j];
+    __syncthreads();
+    for (int k = j + 1 + threadIdx.x; k < n; k += blockDim.x) z[k] = fma(-L[k * n + j], z[j], z[k]);
+    __syncthreads();
+  }
+}
+// x := L^{-T} z in place.
+__device__ void cta_trsv_lt(double *z, const double *L, const double *inv, int n) {
+  for (int j = n - 1; j >= 0; --j) {
+    if (threadIdx.x == 0) z[j] *= inv[j];
+    __syncthreads();
+    for (int k = threadIdx.x; k < j; k += blockDim.x) z[k] = fma(-L[j * n + k], z[j], z[k]);
+    __syncthreads();
+  }
+}
+
+__global__ void k_solve_fwd_level(F64View v, const double *__restrict__ r, int lvl) {
+  const double *invd = v.invd;
+  extern __shared__ double sm[];
+  const int nb = v.nb, nb2 = nb * nb, N = v.N, s = blockIdx.y;
+  double *sz = sm, *sL = sm + nb;
+  const int q = level_task_pos(N, lvl, blockIdx.x);
+  const bool elim = (q < N) && (ctz32(q) == lvl);
+  const size_t sb = (size_t)s * N;
+  const size_t zoff = (sb + (N - q)) * nb;   // natural stage N+1-q of tail s
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    double z = (lvl <= 1) ? r[zoff + i] : v.zt[zoff + i];
+    if (lvl >= 1) {
+      const int h = 1 << (lvl - 1);
+      int pl = 0, pr = 0;
+      if (q < N) {
+        pl = q - h;
+        if (q + h <= N - 1) pr = q + h;
+      } else {
+        const int m = ((N - 1) >> (lvl - 1)) << (lvl - 1);
+        if (ctz32(m) == lvl - 1) pl = m;
+      }
+      if (pl) {
+        const double *Lb = v.Lr + (sb + (N - pl)) * nb2 + i * nb;
+        const double *yp = v.y + (sb + (N - pl)) * nb;
+        for (int k = 0; k < nb; ++k) z = fma(-Lb[k], yp[k], z);
+      }
+      if (pr) {
+        const double *Lb = v.Ll + (sb + (N - pr)) * nb2 + i * nb;
+        const double *yp = v.y + (sb + (N - pr)) * nb;
+        for (int k = 0; k < nb; ++k) z = fma(-Lb[k], yp[k], z);
+      }
+    }
+    sz[i] = z;
+  }
+  if (!elim) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) v.zt[zoff + i] = sz[i];
+    return;
+  }
+  cta_copy(sL, v.Ld + (sb + (N - q)) * nb2, nb2);
+  __syncthreads();
+  cta_trsv_l(sz, sL, invd + zoff, nb);
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) v.y[zoff + i] = sz[i];
+}
+
+// x_1 forward: last update, y_1 = L_{i,1}^{-1} z, t_i = F_{i,1} y_1.
+__global__ void k_solve_x1_fwd(F64View v, const double *__restrict__ r) {
+  const double *invd = v.invd;
+  extern __shared__ double sm[];
+  const int nb = v.nb, nb2 = nb * nb, N = v.N, nr = v.nr, s = blockIdx.x, Lc = v.Lc;
+  double *sz = sm, *sL = sm + nb;
+  const size_t sb = (size_t)s * N;
+  const size_t zoff = sb * nb;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    double z = (Lc <= 1) ? r[zoff + i] : v.zt[zoff + i];
+    if (Lc >= 1) {
+      const int m = 1 << (Lc - 1);
+      const double *Lb = v.Lr + (sb + (N - m)) * nb2 + i * nb;
+      const double *yp = v.y + (sb + (N - m)) * nb;
+      for (int k = 0; k < nb; ++k) z = fma(-Lb[k], yp[k], z);
+    }
+    sz[i] = z;
+  }
+  cta_copy(sL, v.Ld + sb * nb2, nb2);
+  __syncthreads();
+  cta_trsv_l(sz, sL, invd + zoff, nb);
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) v.y[zoff + i] = sz[i];
+  const double *Fs = v.F + (size_t)s * nr * nb;
+  for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+    double acc = 0.0;
+    for (int k = 0; k < nb; ++k) acc = fma(Fs[i * nb + k], sz[k], acc);
+    v.tb[(size_t)s * nr + i] = acc;
+  }
+}
+
+// Root: r~_0 = r_0 - sum_i t_i (one CTA per component, fixed order); the
+// last CTA solves L_R L_R^T x_0 = r~_0 and writes x_0.
+__global__ void k_solve_root(F64View v, const double *__restrict__ r, double *__restrict__ x,
+                             double *__restrict__ r0t) {
+  __shared__ double red[256];
+  __shared__ double sR[64 * 64 + 64 + 64];
+  __shared__ int last;
+  const int nr = v.nr, S = v.S, i = blockIdx.x;
+  const size_t n0 = (size_t)S * v.N * v.nb;
+  double acc = 0.0;
+  for (int s = threadIdx.x; s < S; s += blockDim.x) acc += v.tb[(size_t)s * nr + i];
+  const double tot = cta_sum(acc, red);
+  if (threadIdx.x == 0) {
+    r0t[i] = r[n0 + i] - tot;
+    __threadfence();
+    last = (atomicAdd(&v.tickets[1], 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double *sL = sR, *sz = sR + nr * nr, *sInv = sz + nr;
+  for (int e = threadIdx.x; e < nr * nr; e += blockDim.x) sL[e] = __ldcg(v.LR + e);
+  for (int e = threadIdx.x; e < nr; e += blockDim.x) sz[e] = __ldcg(r0t + e);
+  __syncthreads();
+  for (int e = threadIdx.x; e < nr; e += blockDim.x) sInv[e] = 1.0 / sL[e * nr + e];
+  __syncthreads();
+  cta_trsv_l(sz, sL, sInv, nr);
+  cta_trsv_lt(sz, sL, sInv, nr);
+  for (int e = threadIdx.x; e < nr; e += blockDim.x) x[n0 + e] = sz[e];
+  if (threadIdx.x == 0) v.tickets[1] = 0u;
+}
+
+// Root propagation y_1 -= F_{i,1}^T x_0 and x_1 = L_{i,1}^{-T} y_1.
+__global__ void k_solve_x1_bwd(F64View v, double *__restrict__ x) {
+  const double *invd = v.invd;
+  extern __shared__ double sm[];
+  const int nb = v.nb, nb2 = nb * nb, N = v.N, nr = v.nr, s = blockIdx.x;
+  double *sz = sm, *sL = sm + nb;
+  const size_t sb = (size_t)s * N;
+  const size_t n0 = (size_t)v.S * N * nb;
+  const double *Fs = v.F + (size_t)s * nr * nb;
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+    double z = v.y[sb * nb + k];
+    for (int i = 0; i < nr; ++i) z = fma(-Fs[i * nb + k], x[n0 + i], z);
+    sz[k] = z;
+  }
+  cta_copy(sL, v.Ld + sb * nb2, nb2);
+  __syncthreads();
+  cta_trsv_lt(sz, sL, invd + sb * nb, nb);
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) x[sb * nb + i] = sz[i];
+}
+
+// Backward substitution of level l: x_q = L_qq^{-T} (y_q - L_{a,q}^T x_a - L_{b,q}^T x_b).
+__global__ void k_solve_bwd_level(F64View v, double *__restrict__ x, int lvl) {
+  const double *invd = v.invd;
+  extern __shared__ double sm[];
+  const int nb = v.nb, nb2 = nb * nb, N = v.N, s = blockIdx.y;
+  double *sz = sm, *sL = sm + nb;
+  const int h = 1 << lvl;
+  const int q = (2 * blockIdx.x + 1) << lvl;
+  const int a = q - h, b = (q + h <= N - 1) ? q + h : N;
+  const size_t sb = (size_t)s * N;
+  const double *La = v.Ll + (sb + (N - q)) * nb2, *Lb = v.Lr + (sb + (N - q)) * nb2;
+  const double *xa = x + (sb + (N - a)) * nb, *xb = x + (sb + (N - b)) * nb;
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+    double z = v.y[(sb + (N - q)) * nb + k];
+    for (int i = 0; i < nb; ++i) z = fma(-Lb[i * nb + k], xb[i], z);
+    if (q > h)
+      for (int i = 0; i < nb; ++i) z = fma(-La[i * nb + k], xa[i], z);
+    sz[k] = z;
+  }
+  cta_copy(sL, v.Ld + (sb + (N - q)) * nb2, nb2);
+  __syncthreads();
+  cta_trsv_lt(sz, sL, invd + (sb + (N - q)) * nb, nb);
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) x[(sb + (N - q)) * nb + i] = sz[i];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (stream-ordered; called directly or under capture)
+// ---------------------------------------------------------------------------
+
+static int factor_threads(int nb) { return nb <= 8 ? 32 : nb <= 16 ? 64 : nb <= 32 ? 128 : 256; }
+static int solve_threads(int nb) { return nb <= 32 ? 32 : 64; }
+
+size_t f64_factor_smem(int nb, int nr) {
+  const int mb = nb > nr ? nb : nr;
+  const size_t b2 = 2 * (size_t)nb * nb > (size_t)nr * nb ? 2 * (size_t)nb * nb : (size_t)nr * nb;
+  return ((size_t)mb * mb + b2 + mb) * sizeof(double);
+}
+
+cudaError_t f64_prepare(int nb, int nr) {
+  const int smem = (int)f64_factor_smem(nb, nr);
+  cudaError_t e = cudaFuncSetAttribute(k_factor_level, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_factor_x1, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const int ssm = (int)(((size_t)nb * nb + nb) * sizeof(double));
+  for (const void *f : {(const void *)k_solve_fwd_level, (const void *)k_solve_x1_fwd,
+                        (const void *)k_solve_x1_bwd, (const void *)k_solve_bwd_level}) {
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, ssm);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaFuncSetAttribute(k_factor_root, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(((size_t)nr * nr + nr) * sizeof(double)));
+}
+
+void f64_launch_factor(const F64View &v, cudaStream_t st) {
+  const int T = factor_threads(v.nb);
+  const size_t smem = f64_factor_smem(v.nb, v.nr);
+  for (int l = 0; l < v.Lc; ++l) {
+    dim3 grid(level_tasks(v.N, l), v.S);
+    k_factor_level<<<grid, T, smem, st>>>(v, l);
+  }
+  k_factor_x1<<<v.S, T, smem, st>>>(v);
+  const int ne = v.nr * (v.nr + 1) / 2;
+  k_factor_root<<<ne, 256, ((size_t)v.nr * v.nr + v.nr) * sizeof(double), st>>>(v);
+}
+
+void f64_launch_solve(const F64View &v, const double *r, double *x, double *r0t, cudaStream_t st) {
+  const int T = solve_threads(v.nb);
+  const size_t smem = ((size_t)v.nb * v.nb + v.nb) * sizeof(double);
+  for (int l = 0; l < v.Lc; ++l) {
+    dim3 grid(level_tasks(v.N, l), v.S);
+    k_solve_fwd_level<<<grid, T, smem, st>>>(v, r, l);
+  }
+  k_solve_x1_fwd<<<v.S, T, smem, st>>>(v, r);
+  k_solve_root<<<v.nr, 256, 0, st>>>(v, r, x, r0t);
+  k_solve_x1_bwd<<<v.S, T, smem, st>>>(v, x);
+  for (int l = v.Lc - 1; l >= 0; --l) {
+    dim3 grid(level_elims(v.N, l), v.S);
+    k_solve_bwd_level<<<grid, T, smem, st>>>(v, x, l);
+  }
+}
+
+}  // namespace bm

@@ -1,0 +1,89 @@
+// Internal definitions shared by the CUDA translation units of the library.
+//
+// Indexing of the tail permutation (Sec. IV-A). A tail of N stages is read as
+// a chain of positions p = 1..N with p = N + 1 - k for natural 1-based stage
+// k: Omega_i reverses the stages, positions 1..N-1 carry (x_N, ..., x_2), on
+// which Gamma_{N-1} acts, and position N is x_1, kept last. Gamma_{N-1}
+// (Sec. II) eliminates first every other position starting with the first
+// (the odd ones), then recurses on the rest, so position p belongs to level
+// ctz(p) and the chain has Lc = bit_length(N-1) levels. At level l the chain
+// still holds the multiples of 2^l and x_1; the eliminated position p (an
+// odd multiple of 2^l) has the left neighbour p - 2^l (when p > 2^l) and
+// the right neighbour p + 2^l, or x_1 when p + 2^l > N - 1. Blocks of one
+// level are never neighbours, so they are eliminated concurrently.
+//
+// Every per-stage array of the library is stored by NATURAL stage index
+// k - 1 = N - p, so exported factors line up with the input blocks.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bm.h"
+
+namespace bm {
+
+__host__ __device__ inline int ctz32(int p) {
+#ifdef __CUDA_ARCH__
+  return __ffs(p) - 1;
+#else
+  return __builtin_ctz((unsigned)p);
+#endif
+}
+
+// Number of odd-even levels of the N-1 chain positions.
+__host__ __device__ inline int chain_levels(int N) {
+  int n = N - 1, l = 0;
+  while (n > 0) { ++l; n >>= 1; }
+  return l;
+}
+
+// Tasks of factor/forward launch l: l = 0 -> the odd positions; l >= 1 ->
+// every remaining position (multiples of 2^l) plus x_1.
+__host__ __device__ inline int level_tasks(int N, int l) {
+  return l == 0 ? N / 2 : ((N - 1) >> l) + 1;
+}
+__device__ inline int level_task_pos(int N, int l, int j) {
+  if (l == 0) return 2 * j + 1;
+  int cnt = (N - 1) >> l;
+  return j < cnt ? (j + 1) << l : N;
+}
+// Positions eliminated at level l (odd multiples of 2^l that are <= N-1).
+__host__ __device__ inline int level_elims(int N, int l) {
+  return (((N - 1) >> l) + 1) / 2;
+}
+
+// Device status word (sticky until the next bm_factor).
+struct Status {
+  int code;       // bm_status
+  int scenario;   // 0-based, -1 root
+  int stage;      // 1-based natural stage, 0 root
+  int iters;      // refinement steps
+  double eta;     // refinement backward error
+};
+
+__device__ inline void report_not_spd(Status *st, int scenario, int stage) {
+  if (atomicCAS(&st->code, 0, (int)BM_ERR_NOT_SPD) == 0) {
+    st->scenario = scenario;
+    st->stage = stage;
+  }
+}
+
+// Views passed to the FP64 kernels (by value).
+struct F64View {
+  int S, N, nb, nr, Lc;
+  const double *D, *E, *C, *R;
+  double *Ld, *Ll, *Lr;   // [S][N][nb*nb]
+  double *Dt, *W;         // [S][N][nb*nb] level workspace (updated diagonals, fill couplings)
+  double *F, *U;          // [S][nr*nb], [S][nr*nr]
+  double *LR, *Rt;        // [nr*nr]
+  double *invd;           // [S][N][nb] inverse diagonals 1/(L_pp)_jj of the tail factor
+  double *y, *zt;         // [S][N][nb] solve workspace
+  double *tb;             // [S][nr]
+  unsigned *tickets;      // last-block counters
+  Status *status;
+};
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace bm
