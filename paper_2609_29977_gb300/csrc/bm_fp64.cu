@@ -469,7 +469,14 @@ size_t f64_factor_smem(int nb, int nr) {
   return ((size_t)mb * mb + b2 + mb) * sizeof(double);
 }
 
+// The dynamic shared-memory limit is a per-kernel attribute shared by every
+// handle in the process, so it is always raised to what the largest
+// supported blocks (nb = nr = 64) need; a handle with small blocks must not
+// lower it under another handle's feet.
 cudaError_t f64_prepare(int nb, int nr) {
+  (void)nb;
+  (void)nr;
+  nb = nr = 64;
   const int smem = (int)f64_factor_smem(nb, nr);
   cudaError_t e = cudaFuncSetAttribute(k_factor_level, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;

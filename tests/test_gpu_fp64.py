@@ -255,3 +255,19 @@ def test_fp64_invalid_arguments_are_rejected():
     with pytest.raises(bm.BMError):
         solver.solve(r)                      # before any factor
     solver.close()
+
+
+def test_fp64_handles_with_different_block_sizes_coexist():
+    """Analyzing a small-block handle after a large-block one must not break
+    the large one (kernel attributes are process-wide)."""
+    bm = _bm()
+    big = gen(2, 5, 48, 16, seed=31)
+    gb = to_dev(big)
+    h_big = bm.BranchKKTSolver(2, 5, 48, 16)
+    h_small = bm.BranchKKTSolver(2, 5, 3, 2)
+    h_big.factor(gb["D"], gb["E"], gb["C"], gb["R"])
+    x = h_big.solve(gb["r"]).cpu().numpy()
+    assert h_big.query()["status"] == 0
+    check_solution(big, x)
+    h_small.close()
+    h_big.close()
