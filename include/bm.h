@@ -169,6 +169,42 @@ bm_status bm_factor_solve_host(bm_handle h, const double *hD, const double *hE,
                                const double *hC, const double *hR, const double *hr,
                                double *hx, void *stream);
 
+/*
+ * Size of the library's fixed device scratch array used by
+ * bm_factor_solve_noalloc (32 MiB). Every GPU that loads the library holds
+ * this much device memory until the process exits.
+ */
+#define BM_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/*
+ * FP64 factor + solve that allocates nothing. The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc (code
+ * running inside an allocator or memory-pool callback, real-time loops that
+ * forbid allocation after start-up, hosts that give the library a fixed
+ * device-memory budget). Instead of handle-owned memory it keeps the
+ * factor and all workspaces of the system in one fixed device array of
+ * BM_NOALLOC_SCRATCH_BYTES that the library defines; it calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *   - Inputs D, E, C, R, r and the output x are device pointers with the
+ *     layouts above; x must not alias r. Result: the same x as bm_analyze +
+ *     bm_factor + bm_solve in BM_PREC_FP64.
+ *   - Systems whose factor and workspaces need more than the array holds
+ *     (about 5 S N nb^2 doubles; e.g. S = N = 64 with nb = 12 fits) are
+ *     rejected with BM_ERR_INVALID_ARG before any work, as are the size
+ *     limits of bm_analyze.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current) and keeps it; make
+ *     that first call before any stream capture.
+ *   - The work is ordered on stream; the call then synchronizes stream and
+ *     returns the device status (BM_ERR_NOT_SPD on a non-positive pivot).
+ *   - All calls share the one array, which keeps the last call's contents:
+ *     two calls whose work overlaps on the GPU (different streams or host
+ *     threads) race on it and must be serialized by the caller.
+ */
+bm_status bm_factor_solve_noalloc(int S, int N, int nb, int nr, const double *D, const double *E,
+                                  const double *C, const double *R, const double *r, double *x,
+                                  void *stream);
+
 /* Frees everything the handle owns (synchronizes its internal stream). */
 void bm_destroy(bm_handle h);
 

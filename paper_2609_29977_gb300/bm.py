@@ -23,7 +23,9 @@ STATUS_NAMES = {0: "BM_OK", 1: "BM_ERR_INVALID_ARG", 2: "BM_ERR_NOT_SPD", 3: "BM
                 7: "BM_ERR_NOT_FACTORED"}
 
 EXPORTED_SYMBOLS = ("bm_version", "bm_status_string", "bm_workspace_bytes", "bm_analyze", "bm_factor",
-                    "bm_solve", "bm_query", "bm_export_factor", "bm_factor_solve_host", "bm_destroy")
+                    "bm_solve", "bm_query", "bm_export_factor", "bm_factor_solve_host", "bm_destroy",
+                    "bm_factor_solve_noalloc")
+BM_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 class bm_desc(ctypes.Structure):
@@ -79,6 +81,8 @@ def _load():
     lib.bm_factor_solve_host.argtypes = [vp, dp, dp, dp, dp, dp, dp, vp]
     lib.bm_destroy.restype = None
     lib.bm_destroy.argtypes = [vp]
+    lib.bm_factor_solve_noalloc.restype = ctypes.c_int
+    lib.bm_factor_solve_noalloc.argtypes = [ctypes.c_int] * 4 + [dp] * 6 + [vp]
     _lib = lib
     return lib
 
@@ -166,6 +170,15 @@ def bm_factor_solve_host(h, D, E, C, R, r, x, stream=None) -> int:
 def bm_destroy(h) -> None:
     if h:
         _load().bm_destroy(h)
+
+
+def bm_factor_solve_noalloc(S, N, nb, nr, D, E, C, R, r, x, stream=None) -> int:
+    """FP64 factor + solve in the library's fixed device scratch array, for
+    callers that cannot allocate device memory; synchronizes the stream and
+    returns the device status code (see include/bm.h)."""
+    return int(_load().bm_factor_solve_noalloc(
+        int(S), int(N), int(nb), int(nr), _ptr(D, "D"), _ptr(E, "E") if E is not None and E.numel() else None,
+        _ptr(C, "C"), _ptr(R, "R"), _ptr(r, "r"), _ptr(x, "x"), _stream(stream)))
 
 
 class BranchKKTSolver:
