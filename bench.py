@@ -104,7 +104,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -265,6 +265,7 @@ def run_gpu(args):
     smi_index = ids[local] if local < len(ids) and ids[local].strip().isdigit() else str(local)
     sampler = ClockSampler(smi_index)
     sampler.start()
+    time.sleep(0.5)   # let nvidia-smi start sampling before the timed region
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -299,7 +300,7 @@ def run_gpu(args):
     for _ in range(2):
         solver.factor_solve_host(pin["D"], pin["E"], pin["C"], pin["R"], pin["r"], xh)
     e2e_ms = []
-    for _ in range(args.steps):
+    for _ in range(min(args.steps, 200)):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -317,7 +318,7 @@ def run_gpu(args):
 
     eta, rel2 = gpu_backward_error(g, x)
     Lc = (w.N - 1).bit_length() if w.N > 1 else 0
-    launches_per_step = (Lc + 2) + (2 * Lc + 3)
+    launches_per_step = solver.launches_per_step()
     fmean = statistics.mean(fac_ms)
     peak_alu = fp64_peak_gflops()
     achieved = fl["factor"] / (fmean * 1e-3) / 1e9
@@ -361,8 +362,8 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32ir"])

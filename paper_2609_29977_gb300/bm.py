@@ -201,6 +201,19 @@ class BranchKKTSolver:
         bm_solve(self.h, r, x, stream)
         return x
 
+    def launches_per_step(self) -> int:
+        """Kernels one bm_factor + one bm_solve launch (FP64 path)."""
+        S, N, nb, nr = self.shape
+        Lc = (N - 1).bit_length() if N > 1 else 0
+        if nb not in (2, 3, 4, 6, 8, 12, 16, 24, 32, 48):
+            return (Lc + 2) + (2 * Lc + 3)
+        top = Lc
+        for lvl in range(Lc):   # first level with at most four positions per tail
+            if (N // 2 if lvl == 0 else ((N - 1) >> lvl) + 1) <= 4:
+                top = lvl
+                break
+        return (top + 2) + 3
+
     def query(self, stream=None) -> dict:
         return bm_query(self.h, stream)
 

@@ -469,6 +469,12 @@ size_t f64_factor_smem(int nb, int nr) {
   return ((size_t)mb * mb + b2 + mb) * sizeof(double);
 }
 
+bool f64_team_supported(int nb);
+cudaError_t f64_team_prepare();
+void f64_team_launch_tail(const F64View &v, cudaStream_t st);
+bool f64_cluster_solve_supported(int nb);
+void f64_cluster_launch_solve(const F64View &v, const double *r, double *x, double *r0t, cudaStream_t st);
+
 // The dynamic shared-memory limit is a per-kernel attribute shared by every
 // handle in the process, so it is always raised to what the largest
 // supported blocks (nb = nr = 64) need; a handle with small blocks must not
@@ -488,23 +494,39 @@ cudaError_t f64_prepare(int nb, int nr) {
     e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, ssm);
     if (e != cudaSuccess) return e;
   }
-  return cudaFuncSetAttribute(k_factor_root, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(((size_t)nr * nr + nr) * sizeof(double)));
+  e = cudaFuncSetAttribute(k_factor_root, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(((size_t)nr * nr + nr) * sizeof(double)));
+  if (e != cudaSuccess) return e;
+  return f64_team_prepare();
 }
 
+// Block sizes with compile-time kernels (bm_fp64_team.cu) use those; any
+// other nb runs the runtime-size kernels above.
 void f64_launch_factor(const F64View &v, cudaStream_t st) {
-  const int T = factor_threads(v.nb);
-  const size_t smem = f64_factor_smem(v.nb, v.nr);
-  for (int l = 0; l < v.Lc; ++l) {
-    dim3 grid(level_tasks(v.N, l), v.S);
-    k_factor_level<<<grid, T, smem, st>>>(v, l);
+  if (f64_team_supported(v.nb)) {
+    f64_team_launch_tail(v, st);
+  } else {
+    const int T = factor_threads(v.nb);
+    const size_t smem = f64_factor_smem(v.nb, v.nr);
+    for (int l = 0; l < v.Lc; ++l) {
+      dim3 grid(level_tasks(v.N, l), v.S);
+      k_factor_level<<<grid, T, smem, st>>>(v, l);
+    }
+    k_factor_x1<<<v.S, T, smem, st>>>(v);
   }
-  k_factor_x1<<<v.S, T, smem, st>>>(v);
   const int ne = v.nr * (v.nr + 1) / 2;
   k_factor_root<<<ne, 256, ((size_t)v.nr * v.nr + v.nr) * sizeof(double), st>>>(v);
 }
 
+void f64_launch_solve_root(const F64View &v, const double *r, double *x, double *r0t, cudaStream_t st) {
+  k_solve_root<<<v.nr, 256, 0, st>>>(v, r, x, r0t);
+}
+
 void f64_launch_solve(const F64View &v, const double *r, double *x, double *r0t, cudaStream_t st) {
+  if (f64_cluster_solve_supported(v.nb)) {
+    f64_cluster_launch_solve(v, r, x, r0t, st);
+    return;
+  }
   const int T = solve_threads(v.nb);
   const size_t smem = ((size_t)v.nb * v.nb + v.nb) * sizeof(double);
   for (int l = 0; l < v.Lc; ++l) {

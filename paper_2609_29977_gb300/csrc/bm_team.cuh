@@ -1,0 +1,197 @@
+// Team-level building blocks for the tail kernels.
+//
+// A "team" is TEAM consecutive threads of a CTA that together process one
+// task (one chain position of one tail). TEAM < 32 packs several teams into
+// a warp: their single-lane steps (the pivot reciprocal square roots of the
+// Cholesky) then execute in the same warp instruction, which matters on
+// GB300 where the FP64 pipe charges a full warp instruction whatever the
+// number of active lanes. TEAM >= 64 spreads one task over several warps
+// (several SM sub-partitions) to shorten its dependent chains when a level
+// has few tasks. Teams synchronize with __syncwarp(mask) or a named barrier.
+//
+// Blocks are NB x NB, row-major in shared memory with row stride NB; NB is a
+// compile-time constant so every loop below has a static trip count.
+#pragma once
+
+#include <math.h>
+
+#include "bm_internal.cuh"
+
+namespace bm {
+
+template <int TEAM>
+struct Team {
+  int lane, id;
+  unsigned mask;
+  __device__ __forceinline__ Team() {
+    lane = threadIdx.x % TEAM;
+    id = threadIdx.x / TEAM;
+    if (TEAM < 32)
+      mask = ((1u << TEAM) - 1u) << ((threadIdx.x & 31) / TEAM * TEAM);
+    else
+      mask = 0xffffffffu;
+  }
+  __device__ __forceinline__ void sync() const {
+    if (TEAM < 32)
+      __syncwarp(mask);
+    else if (TEAM == 32)
+      __syncwarp();
+    else
+      asm volatile("bar.sync %0, %1;" ::"r"(id + 1), "r"(TEAM) : "memory");
+  }
+};
+
+// Lower-triangle element e -> (i, j), j <= i (FP32 and integer ops only).
+__device__ __forceinline__ void tri_index(int e, int &i, int &j) {
+  int t = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+  t += ((t + 1) * (t + 2) / 2 <= e);
+  t -= (t * (t + 1) / 2 > e);
+  i = t;
+  j = e - t * (t + 1) / 2;
+}
+
+template <typename T>
+__device__ __forceinline__ T fma_t(T a, T b, T c);
+template <>
+__device__ __forceinline__ double fma_t<double>(double a, double b, double c) { return fma(a, b, c); }
+template <>
+__device__ __forceinline__ float fma_t<float>(float a, float b, float c) { return fmaf(a, b, c); }
+
+template <typename T>
+__device__ __forceinline__ T rsqrt_t(T x);
+template <>
+__device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
+template <>
+__device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+
+// d > 0 and finite, tested on the bit pattern with integer instructions
+// (positive IEEE values order like their bit patterns; NaN and -0 fail).
+template <typename T>
+__device__ __forceinline__ bool pivot_ok(T d);
+template <>
+__device__ __forceinline__ bool pivot_ok<double>(double d) {
+  const long long b = __double_as_longlong(d);
+  return b > 0ll && b < 0x7ff0000000000000ll;
+}
+template <>
+__device__ __forceinline__ bool pivot_ok<float>(float d) {
+  const int b = __float_as_int(d);
+  return b > 0 && b < 0x7f800000;
+}
+
+// Programmatic dependent launch: wait for the preceding kernel's results /
+// let the next kernel start its launch. Both are no-ops without PDL.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <int TEAM, int N, typename T>
+__device__ __forceinline__ void team_copy(const Team<TEAM> &tm, T *__restrict__ dst, const T *__restrict__ src) {
+#pragma unroll
+  for (int i = tm.lane; i < N; i += TEAM) dst[i] = src[i];
+}
+// dst (NB x NB) := src^T
+template <int TEAM, int NB, typename T>
+__device__ __forceinline__ void team_copy_t(const Team<TEAM> &tm, T *__restrict__ dst, const T *__restrict__ src) {
+#pragma unroll
+  for (int e = tm.lane; e < NB * NB; e += TEAM) {
+    const int i = e / NB, j = e - i * NB;
+    dst[j * NB + i] = src[e];
+  }
+}
+template <int TEAM, int N, typename T>
+__device__ __forceinline__ void team_zero(const Team<TEAM> &tm, T *dst) {
+#pragma unroll
+  for (int i = tm.lane; i < N; i += TEAM) dst[i] = T(0);
+}
+template <int TEAM, int NB, typename T>
+__device__ __forceinline__ void team_store_lower(const Team<TEAM> &tm, T *__restrict__ g, const T *__restrict__ s) {
+#pragma unroll
+  for (int e = tm.lane; e < NB * NB; e += TEAM) {
+    const int i = e / NB, j = e - i * NB;
+    g[e] = (j <= i) ? s[e] : T(0);
+  }
+}
+
+// lower(sD) -= X X^T (+ Y Y^T when Y != null).
+template <int TEAM, int NB, typename T>
+__device__ __forceinline__ void team_syrk_sub(const Team<TEAM> &tm, T *sD, const T *X, const T *Y) {
+  constexpr int NE = NB * (NB + 1) / 2;
+#pragma unroll 1
+  for (int e = tm.lane; e < NE; e += TEAM) {
+    int i, j;
+    tri_index(e, i, j);
+    T acc = sD[i * NB + j];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) acc = fma_t<T>(-X[i * NB + k], X[j * NB + k], acc);
+    if (Y) {
+#pragma unroll
+      for (int k = 0; k < NB; ++k) acc = fma_t<T>(-Y[i * NB + k], Y[j * NB + k], acc);
+    }
+    sD[i * NB + j] = acc;
+  }
+}
+
+// In-place lower Cholesky of sA; sInv[j] = 1/L_jj. A non-positive or
+// non-finite pivot is replaced by 1; returns 1 + its column, 0 if none.
+template <int TEAM, int NB, typename T>
+__device__ __forceinline__ int team_chol(const Team<TEAM> &tm, T *sA, T *sInv) {
+  int fail = 0;
+#pragma unroll 1
+  for (int j = 0; j < NB; ++j) {
+    if (tm.lane == 0) {
+      T d = sA[j * NB + j];
+      if (!pivot_ok(d)) {
+        if (!fail) fail = j + 1;
+        d = T(1);
+      }
+      const T r = rsqrt_t<T>(d);
+      sA[j * NB + j] = d * r;
+      sInv[j] = r;
+    }
+    tm.sync();
+    const T r = sInv[j];
+    for (int i = j + 1 + tm.lane; i < NB; i += TEAM) sA[i * NB + j] *= r;
+    tm.sync();
+    const int m = NB - 1 - j, ne = m * (m + 1) / 2;
+    for (int e = tm.lane; e < ne; e += TEAM) {
+      int a, b;
+      tri_index(e, a, b);
+      const int i = j + 1 + a, k = j + 1 + b;
+      sA[i * NB + k] = fma_t<T>(-sA[i * NB + j], sA[k * NB + j], sA[i * NB + k]);
+    }
+    tm.sync();
+  }
+  return fail;
+}
+
+// X (M x NB) := X L^{-T}, with the inverse diagonal of L in inv.
+template <int TEAM, int NB, typename T>
+__device__ __forceinline__ void team_trsm_lt(const Team<TEAM> &tm, T *X, int M, const T *L, const T *inv) {
+#pragma unroll 1
+  for (int j = 0; j < NB; ++j) {
+    const T r = inv[j];
+    for (int row = tm.lane; row < M; row += TEAM) X[row * NB + j] *= r;
+    tm.sync();
+    const int cols = NB - 1 - j, ne = M * cols;
+    for (int e = tm.lane; e < ne; e += TEAM) {
+      const int row = e / cols, k = j + 1 + (e - row * cols);
+      X[row * NB + k] = fma_t<T>(-X[row * NB + j], L[k * NB + j], X[row * NB + k]);
+    }
+    tm.sync();
+  }
+}
+
+// out (NB x NB, global) := -A B^T.
+template <int TEAM, int NB, typename T>
+__device__ __forceinline__ void team_gemm_nt_neg(const Team<TEAM> &tm, T *__restrict__ out, const T *A, const T *B) {
+#pragma unroll 1
+  for (int e = tm.lane; e < NB * NB; e += TEAM) {
+    const int i = e / NB, j = e - i * NB;
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < NB; ++k) acc = fma_t<T>(-A[i * NB + k], B[j * NB + k], acc);
+    out[e] = acc;
+  }
+}
+
+}  // namespace bm
