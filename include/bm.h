@@ -205,6 +205,16 @@ bm_status bm_factor_solve_noalloc(int S, int N, int nb, int nr, const double *D,
                                   const double *C, const double *R, const double *r, double *x,
                                   void *stream);
 
+/*
+ * Rounds n FP64 values to FP32, to nearest with ties to even, using the same
+ * integer-instruction rounding that the BM_PREC_FP32_IR path applies to the
+ * FP64 input blocks as it loads them (the hardware conversion instruction
+ * runs on the FP64 pipe of this GPU). src, dst: device arrays of n
+ * elements. Asynchronous on stream. The paper has no counterpart; it is
+ * exposed so that the rounding can be checked against the hardware's.
+ */
+bm_status bm_round_to_fp32(const double *src, float *dst, size_t n, void *stream);
+
 /* Frees everything the handle owns (synchronizes its internal stream). */
 void bm_destroy(bm_handle h);
 

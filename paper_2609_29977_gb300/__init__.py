@@ -7,10 +7,10 @@ package does not load the library; the first call does, and raises if the
 library was not built (``python -c "import __graft_entry__ as g; g.build()"``).
 """
 from .bm import (BM_FLAG_NO_GRAPH, BM_PREC_FP32_IR, BM_PREC_FP64, BMError, BranchKKTSolver, bm_analyze,
-                 bm_destroy, bm_export_factor, bm_factor, bm_factor_solve_host, bm_factor_solve_noalloc, bm_query, bm_solve,
+                 bm_destroy, bm_export_factor, bm_factor, bm_factor_solve_host, bm_factor_solve_noalloc, bm_query, bm_round_to_fp32, bm_solve,
                  bm_status_string, bm_version, bm_workspace_bytes, library_path)
 
 __all__ = ["BranchKKTSolver", "BMError", "bm_analyze", "bm_factor", "bm_solve", "bm_query",
-           "bm_export_factor", "bm_factor_solve_host", "bm_factor_solve_noalloc", "bm_destroy", "bm_workspace_bytes",
+           "bm_export_factor", "bm_factor_solve_host", "bm_factor_solve_noalloc", "bm_round_to_fp32", "bm_destroy", "bm_workspace_bytes",
            "bm_version", "bm_status_string", "library_path", "BM_PREC_FP64", "BM_PREC_FP32_IR",
            "BM_FLAG_NO_GRAPH"]

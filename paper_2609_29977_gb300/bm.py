@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "BM_OK", 1: "BM_ERR_INVALID_ARG", 2: "BM_ERR_NOT_SPD", 3: "BM
 
 EXPORTED_SYMBOLS = ("bm_version", "bm_status_string", "bm_workspace_bytes", "bm_analyze", "bm_factor",
                     "bm_solve", "bm_query", "bm_export_factor", "bm_factor_solve_host", "bm_destroy",
-                    "bm_factor_solve_noalloc")
+                    "bm_factor_solve_noalloc", "bm_round_to_fp32")
 BM_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -81,6 +81,8 @@ def _load():
     lib.bm_factor_solve_host.argtypes = [vp, dp, dp, dp, dp, dp, dp, vp]
     lib.bm_destroy.restype = None
     lib.bm_destroy.argtypes = [vp]
+    lib.bm_round_to_fp32.restype = ctypes.c_int
+    lib.bm_round_to_fp32.argtypes = [dp, dp, ctypes.c_size_t, vp]
     lib.bm_factor_solve_noalloc.restype = ctypes.c_int
     lib.bm_factor_solve_noalloc.argtypes = [ctypes.c_int] * 4 + [dp] * 6 + [vp]
     _lib = lib
@@ -181,6 +183,15 @@ def bm_factor_solve_noalloc(S, N, nb, nr, D, E, C, R, r, x, stream=None) -> int:
         _ptr(C, "C"), _ptr(R, "R"), _ptr(r, "r"), _ptr(x, "x"), _stream(stream)))
 
 
+def bm_round_to_fp32(src, dst, stream=None) -> None:
+    """Round a float64 device tensor into a float32 device tensor (same size)."""
+    import torch
+    if dst.dtype != torch.float32 or not dst.is_cuda or not dst.is_contiguous() or dst.numel() != src.numel():
+        raise ValueError("dst must be a contiguous float32 CUDA tensor of src's size")
+    _check(_load().bm_round_to_fp32(_ptr(src, "src"), ctypes.c_void_p(dst.data_ptr()), src.numel(),
+                                    _stream(stream)), "bm_round_to_fp32")
+
+
 class BranchKKTSolver:
     """Owns one bm_handle: analyze once, then factor / solve many times."""
 
@@ -202,8 +213,17 @@ class BranchKKTSolver:
         return x
 
     def launches_per_step(self) -> int:
-        """Kernels one bm_factor + one bm_solve launch (FP64 path)."""
+        """Kernels one bm_factor + one bm_solve launch (an upper bound on the
+        mixed path, whose refinement launches exit at once after convergence)."""
         S, N, nb, nr = self.shape
+        if self.desc.precision == BM_PREC_FP32_IR:
+            Lc = (N - 1).bit_length() if N > 1 else 0
+            top = Lc
+            for lvl in range(Lc):
+                if (N // 2 if lvl == 0 else ((N - 1) >> lvl) + 1) <= 4:
+                    top = lvl
+                    break
+            return (top + 2) + 3 * (self.desc.max_refine + 1)
         Lc = (N - 1).bit_length() if N > 1 else 0
         if nb not in (2, 3, 4, 6, 8, 12, 16, 24, 32, 48):
             return (Lc + 2) + (2 * Lc + 3)

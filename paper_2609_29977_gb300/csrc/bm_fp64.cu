@@ -469,9 +469,6 @@ size_t f64_factor_smem(int nb, int nr) {
   return ((size_t)mb * mb + b2 + mb) * sizeof(double);
 }
 
-bool f64_team_supported(int nb);
-cudaError_t f64_team_prepare();
-void f64_team_launch_tail(const F64View &v, cudaStream_t st);
 bool f64_cluster_solve_supported(int nb);
 void f64_cluster_launch_solve(const F64View &v, const double *r, double *x, double *r0t, cudaStream_t st);
 
@@ -497,14 +494,19 @@ cudaError_t f64_prepare(int nb, int nr) {
   e = cudaFuncSetAttribute(k_factor_root, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(((size_t)nr * nr + nr) * sizeof(double)));
   if (e != cudaSuccess) return e;
-  return f64_team_prepare();
+  return tail_factor_prepare();
 }
 
 // Block sizes with compile-time kernels (bm_fp64_team.cu) use those; any
 // other nb runs the runtime-size kernels above.
 void f64_launch_factor(const F64View &v, cudaStream_t st) {
-  if (f64_team_supported(v.nb)) {
-    f64_team_launch_tail(v, st);
+  if (tail_nb_supported(v.nb)) {
+    TailView<double> t;
+    t.S = v.S; t.N = v.N; t.nb = v.nb; t.nr = v.nr; t.Lc = v.Lc;
+    t.D = v.D; t.E = v.E; t.C = v.C; t.R = v.R;
+    t.Ld = v.Ld; t.Ll = v.Ll; t.Lr = v.Lr; t.Dt = v.Dt; t.W = v.W; t.invd = v.invd;
+    t.F = v.F; t.U = v.U; t.status = v.status;
+    tail_factor_launch<double>(t, st);
   } else {
     const int T = factor_threads(v.nb);
     const size_t smem = f64_factor_smem(v.nb, v.nr);
@@ -516,6 +518,22 @@ void f64_launch_factor(const F64View &v, cudaStream_t st) {
   }
   const int ne = v.nr * (v.nr + 1) / 2;
   k_factor_root<<<ne, 256, ((size_t)v.nr * v.nr + v.nr) * sizeof(double), st>>>(v);
+}
+
+// Root step of the factor for callers that hold raw buffers (mixed path).
+void f64_launch_factor_root_raw(int S, int nr, const double *U, const double *R, double *Rt, double *LR,
+                                unsigned *tickets, Status *status, cudaStream_t st) {
+  F64View v{};
+  v.S = S;
+  v.nr = nr;
+  v.U = const_cast<double *>(U);
+  v.R = R;
+  v.Rt = Rt;
+  v.LR = LR;
+  v.tickets = tickets;
+  v.status = status;
+  const int ne = nr * (nr + 1) / 2;
+  k_factor_root<<<ne, 256, ((size_t)nr * nr + nr) * sizeof(double), st>>>(v);
 }
 
 void f64_launch_solve_root(const F64View &v, const double *r, double *x, double *r0t, cudaStream_t st) {

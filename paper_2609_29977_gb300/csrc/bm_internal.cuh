@@ -84,6 +84,58 @@ struct F64View {
   Status *status;
 };
 
+// View of one system's tail factor for the templated tail kernels
+// (T = double on the FP64 path, float for the tails of the mixed path). The
+// inputs are always FP64; the coupling factor F and local updates U are
+// always FP64.
+template <typename T>
+struct TailView {
+  int S, N, nb, nr, Lc;
+  const double *D, *E, *C, *R;
+  T *Ld, *Ll, *Lr;   // [S][N][nb*nb]
+  T *Dt, *W;         // [S][N][nb*nb] level workspace
+  T *invd;           // [S][N][nb]
+  double *F, *U;     // [S][nr*nb], [S][nr*nr]
+  Status *status;
+};
+
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Block sizes with compile-time tail kernels.
+#define BM_TAIL_NB_LIST(X) X(2) X(3) X(4) X(6) X(8) X(12) X(16) X(24) X(32) X(48)
+
+// First level handled by the per-tail top kernel: the first one with at
+// most four positions per tail (Lc when none).
+inline int top_level(int N) {
+  const int Lc = chain_levels(N);
+  for (int l = 0; l < Lc; ++l) {
+    const int tasks = l == 0 ? N / 2 : ((N - 1) >> l) + 1;
+    if (tasks <= 4) return l;
+  }
+  return Lc;
+}
+
+bool tail_nb_supported(int nb);
+cudaError_t tail_factor_prepare();
+template <typename T>
+void tail_factor_launch(const TailView<T> &v, cudaStream_t st);
+
+// Launch with programmatic stream serialization (PDL): the kernel may begin
+// while its predecessor drains and waits in griddepcontrol.wait.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
 
 }  // namespace bm

@@ -1,14 +1,619 @@
-// Mixed-precision path (FP32 tails, FP64 root and refinement): not built yet.
-#include "bm_internal.cuh"
+// Mixed-precision path (BM_PREC_FP32_IR): FP32 tails, FP64 root, FP64
+// iterative refinement on the full system. Not in the paper; its steps are
+// the paper's (Alg. 1 for the factor, Alg. 2 for each correction solve) with
+// the tail blocks held in FP32.
+//
+// Factor: the tail factor of Alg. 1 steps 1-3 in FP32 (bm_tail_factor.cuh,
+// T = float); F_{i,1} and U_i = F_{i,1} F_{i,1}^T in FP64 from the FP32
+// L_{i,1}; the root reduction R - sum U_i and L_R = chol in FP64.
+//
+// Solve: x_0 = 0, rho_0 = r; for k = 0..max_refine:
+//   d = M^{-1} rho_k  (Alg. 2 with FP32 tails and an FP64 root step),
+//   x += d (FP64), rho_{k+1} = r - K x (FP64, from the caller's D, E, C, R),
+//   eta = ||rho||_inf / (||K||_inf ||x||_inf + ||r||_inf); stop when eta <= tol.
+// Each iteration is three launches: forward tail substitution whose last CTA
+// does the root step, backward tail substitution fused with x += d, and the
+// residual whose last CTA evaluates eta and raises a device flag once
+// converged; every later launch checks the flag first and returns, so the
+// whole unrolled loop is one CUDA graph with no host round trip.
+#include <cuda_runtime.h>
+
+#include <new>
+
+#include "bm_tail_factor.cuh"
 
 namespace bm {
-struct MixedState {};
-size_t mixed_bytes(int, int, int, int) { return 0; }
-cudaError_t mixed_prepare(int, int) { return cudaErrorNotSupported; }
-MixedState *mixed_create(int, int, int, int, void *, size_t, Status *, unsigned *) { return nullptr; }
-void mixed_destroy(MixedState *) {}
-void mixed_launch_factor(MixedState *, const double *, const double *, const double *, const double *,
-                         cudaStream_t) {}
-void mixed_launch_solve(MixedState *, const double *, double *, int, double, cudaStream_t) {}
-void mixed_launch_export(MixedState *, double *, double *, double *, double *, double *, cudaStream_t) {}
+
+struct IRCtl {
+  int converged;                  // set by the residual kernel once eta <= tol
+  int iters;                      // corrections applied in the last solve
+  unsigned long long rmax, xmax;  // |rho|_inf, |x|_inf of the running iteration (bit patterns)
+  unsigned long long kmax, bmax;  // ||K||_inf (computed once per factor), ||r||_inf (once per solve)
+  int knorm_valid;
+  int pad;
+  double eta;
+};
+
+struct MixedState {
+  int S, N, nb, nr, Lc;
+  float *Ld, *Ll, *Lr, *Dt, *W, *invd;   // FP32 tail factor and level workspace
+  double *F, *U, *LR, *Rt;               // FP64 root parts
+  float *y, *zt;                         // [S][N][nb] solve vectors (y is overwritten by the correction)
+  double *tb;                            // [S][nr]
+  double *d0;                            // [nr] root correction
+  double *rho;                           // [n] residual
+  IRCtl *ctl;
+  Status *status;
+  unsigned *tickets;
+  const double *D, *E, *C, *R;           // inputs of the last factor
+};
+
+namespace {
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+// |x| rounded down to FP32, from the bit pattern with integer instructions
+// (for the row sums of |K|; only used for the norm in the stopping test).
+__device__ __forceinline__ float abs_f32_approx(double x) {
+  const unsigned hi = (unsigned)(__double_as_longlong(x) >> 32) & 0x7fffffffu;
+  const int e = (int)(hi >> 20) - 1023 + 127;
+  if (e <= 0) return 0.0f;
+  if (e >= 255) return __uint_as_float(0x7f7fffffu);
+  return __uint_as_float(((unsigned)e << 23) | ((hi & 0xfffffu) << 3));
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+template <int NB>
+struct MCfg {
+  static constexpr int TS = NB <= 4 ? 4 : NB <= 8 ? 8 : NB <= 16 ? 16 : NB <= 32 ? 32 : 64;
+  static constexpr int THREADS = 256;
+  static constexpr int TEAMS = THREADS / TS;
+};
+
+__device__ __forceinline__ bool ir_done(const IRCtl *ctl) {
+  return *((volatile const int *)&ctl->converged) != 0;
+}
+
+// Forward substitution of one tail in FP32 (all levels, then x_1 and
+// t_i = F_{i,1} y_1 in FP64); the last CTA of the grid does the root step
+// of Alg. 2 in FP64 and stores the root correction d_0 (and x_0 += d_0).
+template <int NB>
+__global__ void __launch_bounds__(256) k_mixed_fwd(MixedState m, const double *__restrict__ rhs, double *x, int iter,
+                                                    int CS) {
+  constexpr int TS = MCfg<NB>::TS, TEAMS = MCfg<NB>::TEAMS, NB2 = NB * NB;
+  __shared__ float sY[TEAMS][NB];
+  __shared__ double sR[64 * 64 + 64 + 64];
+  __shared__ int last;
+  const Team<TS> tm;
+  pdl_wait();
+  if (ir_done(m.ctl)) return;
+  const int crank = (int)cluster_rank();
+  const int s = blockIdx.x / CS;
+  const int N = m.N, Lc = m.Lc;
+  const size_t sb = (size_t)s * N;
+  const int i = tm.lane;
+  for (int lvl = 0; lvl <= Lc; ++lvl) {
+    const bool lastlvl = lvl == Lc;
+    const int ntask = lastlvl ? 1 : (lvl == 0 ? N / 2 : ((N - 1) >> lvl) + 1);
+    for (int t = crank * TEAMS + tm.id; t < ntask; t += CS * TEAMS) {
+      int q;
+      if (lastlvl) q = N;
+      else if (lvl == 0) q = 2 * t + 1;
+      else {
+        const int cnt = (N - 1) >> lvl;
+        q = t < cnt ? (t + 1) << lvl : N;
+      }
+      const bool elim = lastlvl || (q < N && ctz32(q) == lvl);
+      const size_t zoff = (sb + (N - q)) * NB;
+      float z = 0.0f;
+      if (i < NB) {
+        z = (lvl <= 1) ? d2f_rn(rhs[zoff + i]) : __ldcg(m.zt + zoff + i);
+        if (lvl >= 1) {
+          const int h = 1 << (lvl - 1);
+          int pl = 0, pr = 0;
+          if (q < N) {
+            pl = q - h;
+            if (q + h <= N - 1) pr = q + h;
+          } else {
+            const int mm = ((N - 1) >> (lvl - 1)) << (lvl - 1);
+            if (ctz32(mm) == lvl - 1) pl = mm;
+          }
+          if (pl) {
+            const float *L = m.Lr + (sb + (N - pl)) * NB2 + i * NB;
+            const float *y = m.y + (sb + (N - pl)) * NB;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) z = fmaf(-L[k], __ldcg(y + k), z);
+          }
+          if (pr) {
+            const float *L = m.Ll + (sb + (N - pr)) * NB2 + i * NB;
+            const float *y = m.y + (sb + (N - pr)) * NB;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) z = fmaf(-L[k], __ldcg(y + k), z);
+          }
+        }
+      }
+      if (!elim) {
+        if (i < NB) m.zt[zoff + i] = z;
+        continue;
+      }
+      float Lrow[NB];
+      const float *Ld = m.Ld + (sb + (N - q)) * NB2 + (i < NB ? i : 0) * NB;
+#pragma unroll
+      for (int k = 0; k < NB; ++k) Lrow[k] = Ld[k];
+      const float inv = i < NB ? m.invd[zoff + i] : 0.0f;
+      if (TS <= 32) {
+        const int base = (threadIdx.x & 31) & ~(TS - 1);
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+          if (i == j) z *= inv;
+          const float yj = __shfl_sync(tm.mask, z, base + j);
+          if (i > j && i < NB) z = fmaf(-Lrow[j], yj, z);
+        }
+        if (i < NB) sY[tm.id][i] = z;
+        tm.sync();
+      } else {
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+          if (i == j) {
+            z *= inv;
+            sY[tm.id][j] = z;
+          }
+          tm.sync();
+          if (i > j && i < NB) z = fmaf(-Lrow[j], sY[tm.id][j], z);
+        }
+      }
+      if (i < NB) m.y[zoff + i] = z;
+      if (lastlvl) {
+        tm.sync();
+        const int nr = m.nr;
+        const double *Fs = m.F + (size_t)s * nr * NB;
+        for (int c = i; c < nr; c += TS) {
+          double acc = 0.0;
+#pragma unroll
+          for (int k = 0; k < NB; ++k) acc = fma(Fs[c * NB + k], f2d_exact(sY[tm.id][k]), acc);
+          m.tb[(size_t)s * nr + c] = acc;
+        }
+      }
+      tm.sync();
+    }
+    cluster_sync();
+  }
+  // root step by the last CTA to finish
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&m.tickets[2], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int nr = m.nr, S = m.S;
+  const size_t n0 = (size_t)S * N * NB;
+  double *sL = sR, *sz = sR + nr * nr, *sInv = sz + nr;
+  for (int e = threadIdx.x; e < nr * nr; e += blockDim.x) sL[e] = __ldcg(m.LR + e);
+  // r~_0 = rhs_0 - sum_i t_i, fixed summation order per component
+  for (int c = threadIdx.x; c < nr; c += blockDim.x) {
+    double acc = rhs[n0 + c];
+    for (int t = 0; t < S; ++t) acc -= __ldcg(m.tb + (size_t)t * nr + c);
+    sz[c] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < nr; ++j) {
+      double v = sz[j];
+      for (int k = 0; k < j; ++k) v = fma(-sL[j * nr + k], sz[k], v);
+      sz[j] = v / sL[j * nr + j];
+    }
+    for (int j = nr - 1; j >= 0; --j) {
+      double v = sz[j];
+      for (int k = j + 1; k < nr; ++k) v = fma(-sL[k * nr + j], sz[k], v);
+      sz[j] = v / sL[j * nr + j];
+    }
+    for (int j = 0; j < nr; ++j) {
+      m.d0[j] = sz[j];
+      x[n0 + j] = (iter == 0 ? 0.0 : x[n0 + j]) + sz[j];
+    }
+    m.tickets[2] = 0u;
+  }
+  (void)sInv;
+}
+
+// Backward substitution in FP32 fused with x += d (FP64); the correction of
+// each position overwrites its forward vector y.
+template <int NB>
+__global__ void __launch_bounds__(256) k_mixed_bwd(MixedState m, double *x, int iter, int CS) {
+  constexpr int TS = MCfg<NB>::TS, TEAMS = MCfg<NB>::TEAMS, NB2 = NB * NB;
+  __shared__ float sX[TEAMS][NB];
+  const Team<TS> tm;
+  pdl_wait();
+  if (ir_done(m.ctl)) return;
+  const int crank = (int)cluster_rank();
+  const int s = blockIdx.x / CS;
+  const int N = m.N, Lc = m.Lc, nr = m.nr;
+  const size_t sb = (size_t)s * N;
+  const int i = tm.lane;
+  for (int lvl = Lc; lvl >= 0; --lvl) {
+    const bool first = lvl == Lc;
+    const int ntask = first ? 1 : (((N - 1) >> lvl) + 1) / 2;
+    for (int t = crank * TEAMS + tm.id; t < ntask; t += CS * TEAMS) {
+      const int q = first ? N : (2 * t + 1) << lvl;
+      const size_t zoff = (sb + (N - q)) * NB;
+      float z = 0.0f;
+      if (i < NB) {
+        if (first) {
+          double zd = f2d_exact(m.y[zoff + i]);
+          const double *Fs = m.F + (size_t)s * nr * NB;
+          for (int c = 0; c < nr; ++c) zd = fma(-Fs[c * NB + i], __ldcg(m.d0 + c), zd);
+          z = d2f_rn(zd);
+        } else {
+          z = m.y[zoff + i];
+          const int h = 1 << lvl;
+          const int a = q - h, b = (q + h <= N - 1) ? q + h : N;
+          const float *Lb = m.Lr + (sb + (N - q)) * NB2 + i;
+          const float *db = m.y + (sb + (N - b)) * NB;
+#pragma unroll
+          for (int k = 0; k < NB; ++k) z = fmaf(-Lb[k * NB], __ldcg(db + k), z);
+          if (q > h) {
+            const float *La = m.Ll + (sb + (N - q)) * NB2 + i;
+            const float *da = m.y + (sb + (N - a)) * NB;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) z = fmaf(-La[k * NB], __ldcg(da + k), z);
+          }
+        }
+      }
+      float Lcol[NB];
+      const float *Ld = m.Ld + (sb + (N - q)) * NB2 + (i < NB ? i : 0);
+#pragma unroll
+      for (int k = 0; k < NB; ++k) Lcol[k] = Ld[k * NB];
+      const float inv = i < NB ? m.invd[zoff + i] : 0.0f;
+      if (TS <= 32) {
+        const int base = (threadIdx.x & 31) & ~(TS - 1);
+#pragma unroll
+        for (int j = NB - 1; j >= 0; --j) {
+          if (i == j) z *= inv;
+          const float xj = __shfl_sync(tm.mask, z, base + j);
+          if (i < j) z = fmaf(-Lcol[j], xj, z);
+        }
+      } else {
+#pragma unroll
+        for (int j = NB - 1; j >= 0; --j) {
+          if (i == j) {
+            z *= inv;
+            sX[tm.id][j] = z;
+          }
+          tm.sync();
+          if (i < j) z = fmaf(-Lcol[j], sX[tm.id][j], z);
+        }
+      }
+      if (i < NB) {
+        m.y[zoff + i] = z;
+        const double dz = f2d_exact(z);
+        x[zoff + i] = iter == 0 ? dz : x[zoff + i] + dz;
+      }
+      tm.sync();
+    }
+    cluster_sync();
+  }
+}
+
+// rho = r - K x in FP64 with the norms of the stopping test; one team of
+// NB lanes per (tail, stage) block row (row i of the block per lane), one
+// more CTA-strided pass over the root rows. The last CTA evaluates eta.
+template <int NB>
+__global__ void __launch_bounds__(256) k_mixed_residual(MixedState m, const double *__restrict__ r,
+                                                         const double *__restrict__ x, int iter, int max_iter,
+                                                         double tol) {
+  constexpr int TS = MCfg<NB>::TS, TEAMS = MCfg<NB>::TEAMS, NB2 = NB * NB;
+  __shared__ int last;
+  const Team<TS> tm;
+  pdl_wait();
+  if (ir_done(m.ctl)) return;
+  const int N = m.N, S = m.S, nr = m.nr;
+  const size_t n0 = (size_t)S * N * NB;
+  const bool knorm = !m.ctl->knorm_valid;
+  const double *D = m.D, *E = m.E, *C = m.C, *R = m.R;
+  const double *x0 = x + n0;
+  unsigned long long rmax = 0, xmax = 0, bmax = 0;
+  float kmax = 0.0f;
+  const long nrow = (long)S * N;
+  const int i = tm.lane;
+  for (long br = (long)blockIdx.x * TEAMS + tm.id; br < nrow; br += (long)gridDim.x * TEAMS) {
+    if (i >= NB) continue;
+    const int s = (int)(br / N), k = (int)(br - (long)s * N);
+    const size_t off = (size_t)br * NB;
+    const double *Dk = D + (size_t)br * NB2;
+    const double *xk = x + off;
+    double acc = r[off + i];
+    float ks = 0.0f;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const double kij = j <= i ? Dk[i * NB + j] : Dk[j * NB + i];
+      acc = fma(-kij, xk[j], acc);
+      if (knorm) ks += abs_f32_approx(kij);
+    }
+    if (k > 0) {   // block (k, k-1) = E_k (1-based stage k+1)
+      const double *Ek = E + ((size_t)s * (N - 1) + (k - 1)) * NB2 + i * NB;
+      const double *xp = xk - NB;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        acc = fma(-Ek[j], xp[j], acc);
+        if (knorm) ks += abs_f32_approx(Ek[j]);
+      }
+    }
+    if (k + 1 < N) {   // block (k, k+1) = E_{k+1}^T
+      const double *Ek = E + ((size_t)s * (N - 1) + k) * NB2 + i;
+      const double *xn = xk + NB;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        acc = fma(-Ek[j * NB], xn[j], acc);
+        if (knorm) ks += abs_f32_approx(Ek[j * NB]);
+      }
+    }
+    if (k == 0) {   // block (1, root) = C_s^T
+      const double *Cs = C + (size_t)s * nr * NB + i;
+      for (int j = 0; j < nr; ++j) {
+        acc = fma(-Cs[j * NB], x0[j], acc);
+        if (knorm) ks += abs_f32_approx(Cs[j * NB]);
+      }
+    }
+    m.rho[off + i] = acc;
+    const unsigned long long ra = abs_bits(acc), xa = abs_bits(xk[i]);
+    rmax = ra > rmax ? ra : rmax;
+    xmax = xa > xmax ? xa : xmax;
+    if (iter == 0) {
+      const unsigned long long ba = abs_bits(r[off + i]);
+      bmax = ba > bmax ? ba : bmax;
+    }
+    kmax = ks > kmax ? ks : kmax;
+  }
+  // root rows: R x0 + sum_s C_s x_{s,1}, one component per CTA-strided row
+  for (int c = blockIdx.x; c < nr; c += gridDim.x) {
+    double acc = 0.0;
+    float ks = 0.0f;
+    for (long e = threadIdx.x; e < (long)S * NB + nr; e += blockDim.x) {
+      double kv, xv;
+      if (e < (long)S * NB) {
+        const int s = (int)(e / NB), j = (int)(e - (long)s * NB);
+        kv = C[((size_t)s * nr + c) * NB + j];
+        xv = x[(size_t)s * N * NB + j];
+      } else {
+        const int j = (int)(e - (long)S * NB);
+        kv = j <= c ? R[c * nr + j] : R[j * nr + c];
+        xv = x0[j];
+      }
+      acc = fma(kv, xv, acc);
+      if (knorm) ks += abs_f32_approx(kv);
+    }
+    __shared__ double red[256];
+    __shared__ float redf[256];
+    red[threadIdx.x] = acc;
+    redf[threadIdx.x] = ks;
+    for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
+      __syncthreads();
+      if ((int)threadIdx.x < w) {
+        red[threadIdx.x] += red[threadIdx.x + w];
+        redf[threadIdx.x] += redf[threadIdx.x + w];
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double rc = r[n0 + c] - red[0];
+      m.rho[n0 + c] = rc;
+      const unsigned long long ra = abs_bits(rc), xa = abs_bits(x0[c]);
+      rmax = ra > rmax ? ra : rmax;
+      xmax = xa > xmax ? xa : xmax;
+      if (iter == 0) {
+        const unsigned long long ba = abs_bits(r[n0 + c]);
+        bmax = ba > bmax ? ba : bmax;
+      }
+      kmax = redf[0] > kmax ? redf[0] : kmax;
+    }
+    __syncthreads();
+  }
+  rmax = warp_max_u64(rmax);
+  xmax = warp_max_u64(xmax);
+  bmax = warp_max_u64(bmax);
+  unsigned kb = __float_as_uint(kmax);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned w = __shfl_xor_sync(0xffffffffu, kb, o);
+    kb = w > kb ? w : kb;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&m.ctl->rmax, rmax);
+    atomicMax(&m.ctl->xmax, xmax);
+    if (iter == 0) atomicMax(&m.ctl->bmax, bmax);
+    if (knorm) atomicMax(&m.ctl->kmax, (unsigned long long)kb);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&m.tickets[3], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  IRCtl *ctl = m.ctl;
+  const double rn = __longlong_as_double((long long)atomicAdd(&ctl->rmax, 0ull));
+  const double xn = __longlong_as_double((long long)atomicAdd(&ctl->xmax, 0ull));
+  const double bn = __longlong_as_double((long long)atomicAdd(&ctl->bmax, 0ull));
+  const double kn = (double)__uint_as_float((unsigned)atomicAdd(&ctl->kmax, 0ull));
+  const double eta = rn / (kn * xn + bn);
+  ctl->eta = eta;
+  ctl->iters = iter;
+  ctl->knorm_valid = 1;
+  m.status->eta = eta;
+  m.status->iters = iter;
+  if (eta <= tol) {
+    ctl->converged = 1;
+  } else if (iter >= max_iter && m.status->code == 0) {
+    m.status->code = (int)BM_ERR_NOT_CONVERGED;
+  }
+  ctl->rmax = 0ull;
+  ctl->xmax = 0ull;
+  m.tickets[3] = 0u;
+}
+
+// Widen the FP32 tail factor for export.
+__global__ void k_widen(const float *__restrict__ src, double *__restrict__ dst, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = f2d_exact(src[i]);
+}
+
+int pick_cluster(int S) {
+  int cs = 1;
+  while (cs < 8 && S * cs * 2 <= 152) cs <<= 1;
+  return cs;
+}
+
+template <typename... KArgs, typename... Args>
+void launch_cluster(void (*kern)(KArgs...), unsigned grid, unsigned block, int CS, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+template <int NB>
+void launch_iteration(const MixedState &m, const double *r, double *x, int iter, int max_iter, double tol,
+                      cudaStream_t st) {
+  const int CS = pick_cluster(m.S);
+  const unsigned grid = (unsigned)(m.S * CS);
+  const double *rhs = iter == 0 ? r : m.rho;
+  launch_cluster(k_mixed_fwd<NB>, grid, 256, CS, st, m, rhs, x, iter, CS);
+  launch_cluster(k_mixed_bwd<NB>, grid, 256, CS, st, m, x, iter, CS);
+  const long rows = (long)m.S * m.N;
+  long blocks = (rows + MCfg<NB>::TEAMS - 1) / MCfg<NB>::TEAMS;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks < m.nr) blocks = m.nr;
+  launch_pdl(k_mixed_residual<NB>, (unsigned)blocks, 256, 0, st, m, r, (const double *)x, iter, max_iter, tol);
+}
+
+}  // namespace
+
+size_t mixed_bytes(int S, int N, int nb, int nr) {
+  const size_t SN = (size_t)S * N, b2 = (size_t)nb * nb, n = SN * nb + nr;
+  size_t t = 0;
+  t += align_up(SN * b2 * sizeof(float), 256) * 5;          // Ld Ll Lr Dt W
+  t += align_up(SN * nb * sizeof(float), 256) * 3;          // invd y zt
+  t += align_up((size_t)S * nr * nb * sizeof(double), 256); // F
+  t += align_up((size_t)S * nr * nr * sizeof(double), 256); // U
+  t += align_up((size_t)nr * nr * sizeof(double), 256) * 2; // LR Rt
+  t += align_up((size_t)S * nr * sizeof(double), 256);      // tb
+  t += align_up((size_t)nr * sizeof(double), 256);          // d0
+  t += align_up(n * sizeof(double), 256);                   // rho
+  t += align_up(sizeof(IRCtl), 256);
+  return t;
+}
+
+cudaError_t mixed_prepare(int nb, int nr) {
+  (void)nr;
+  if (!tail_nb_supported(nb)) return cudaErrorInvalidValue;
+  return tail_factor_prepare();
+}
+
+MixedState *mixed_create(int S, int N, int nb, int nr, void *base, size_t bytes, Status *status,
+                         unsigned *tickets) {
+  if (bytes < mixed_bytes(S, N, nb, nr)) return nullptr;
+  MixedState *m = new (std::nothrow) MixedState();
+  if (!m) return nullptr;
+  m->S = S; m->N = N; m->nb = nb; m->nr = nr; m->Lc = chain_levels(N);
+  char *p = (char *)base;
+  auto take = [&](size_t b) {
+    void *q = p;
+    p += align_up(b, 256);
+    return q;
+  };
+  const size_t SN = (size_t)S * N, b2 = (size_t)nb * nb, n = SN * nb + nr;
+  m->Ld = (float *)take(SN * b2 * 4); m->Ll = (float *)take(SN * b2 * 4); m->Lr = (float *)take(SN * b2 * 4);
+  m->Dt = (float *)take(SN * b2 * 4); m->W = (float *)take(SN * b2 * 4);
+  m->invd = (float *)take(SN * nb * 4); m->y = (float *)take(SN * nb * 4); m->zt = (float *)take(SN * nb * 4);
+  m->F = (double *)take((size_t)S * nr * nb * 8); m->U = (double *)take((size_t)S * nr * nr * 8);
+  m->LR = (double *)take((size_t)nr * nr * 8); m->Rt = (double *)take((size_t)nr * nr * 8);
+  m->tb = (double *)take((size_t)S * nr * 8); m->d0 = (double *)take((size_t)nr * 8);
+  m->rho = (double *)take(n * 8);
+  m->ctl = (IRCtl *)take(sizeof(IRCtl));
+  m->status = status;
+  m->tickets = tickets;
+  if (cudaMemset(m->ctl, 0, sizeof(IRCtl)) != cudaSuccess) {
+    delete m;
+    return nullptr;
+  }
+  return m;
+}
+
+void mixed_destroy(MixedState *m) { delete m; }
+
+// Root step of the factor, shared with the FP64 path (bm_fp64.cu).
+void f64_launch_factor_root_raw(int S, int nr, const double *U, const double *R, double *Rt, double *LR,
+                                unsigned *tickets, Status *status, cudaStream_t st);
+
+void mixed_launch_factor(MixedState *m, const double *D, const double *E, const double *C, const double *R,
+                         cudaStream_t st) {
+  m->D = D; m->E = E; m->C = C; m->R = R;
+  TailView<float> t;
+  t.S = m->S; t.N = m->N; t.nb = m->nb; t.nr = m->nr; t.Lc = m->Lc;
+  t.D = D; t.E = E; t.C = C; t.R = R;
+  t.Ld = m->Ld; t.Ll = m->Ll; t.Lr = m->Lr; t.Dt = m->Dt; t.W = m->W; t.invd = m->invd;
+  t.F = m->F; t.U = m->U; t.status = m->status;
+  cudaMemsetAsync(&m->ctl->knorm_valid, 0, sizeof(int), st);
+  cudaMemsetAsync(&m->ctl->kmax, 0, sizeof(unsigned long long), st);
+  tail_factor_launch<float>(t, st);
+  f64_launch_factor_root_raw(m->S, m->nr, m->U, R, m->Rt, m->LR, m->tickets, m->status, st);
+}
+
+void mixed_launch_solve(MixedState *m, const double *r, double *x, int max_refine, double tol, cudaStream_t st) {
+  // reset the per-solve control words (keep ||K|| of the factor)
+  cudaMemsetAsync(&m->ctl->converged, 0, 2 * sizeof(int), st);
+  cudaMemsetAsync(&m->ctl->rmax, 0, 2 * sizeof(unsigned long long), st);
+  cudaMemsetAsync(&m->ctl->bmax, 0, sizeof(unsigned long long), st);
+  for (int it = 0; it <= max_refine; ++it) {
+    switch (m->nb) {
+#define X(n)                                                  \
+  case n:                                                     \
+    launch_iteration<n>(*m, r, x, it, max_refine, tol, st);   \
+    break;
+      BM_TAIL_NB_LIST(X)
+#undef X
+    }
+  }
+}
+
+int mixed_launches_per_solve(int max_refine) { return 3 * (max_refine + 1); }
+
+void mixed_launch_export(MixedState *m, double *Ld, double *Ll, double *Lr, double *F, double *LR,
+                         cudaStream_t st) {
+  const size_t n = (size_t)m->S * m->N * m->nb * m->nb;
+  if (Ld) k_widen<<<1024, 256, 0, st>>>(m->Ld, Ld, n);
+  if (Ll) k_widen<<<1024, 256, 0, st>>>(m->Ll, Ll, n);
+  if (Lr) k_widen<<<1024, 256, 0, st>>>(m->Lr, Lr, n);
+  if (F) cudaMemcpyAsync(F, m->F, (size_t)m->S * m->nr * m->nb * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  if (LR) cudaMemcpyAsync(LR, m->LR, (size_t)m->nr * m->nr * sizeof(double), cudaMemcpyDeviceToDevice, st);
+}
+
 }  // namespace bm

@@ -1,0 +1,17 @@
+// Explicit instantiations of the tail factorization kernels (float, nb in [2, 3, 4, 6, 8]).
+#include "bm_tail_factor.cuh"
+
+namespace bm {
+namespace tail {
+template void launch_tail_nb<float, 2>(const TailView<float> &, cudaStream_t);
+template cudaError_t prepare_nb<float, 2>();
+template void launch_tail_nb<float, 3>(const TailView<float> &, cudaStream_t);
+template cudaError_t prepare_nb<float, 3>();
+template void launch_tail_nb<float, 4>(const TailView<float> &, cudaStream_t);
+template cudaError_t prepare_nb<float, 4>();
+template void launch_tail_nb<float, 6>(const TailView<float> &, cudaStream_t);
+template cudaError_t prepare_nb<float, 6>();
+template void launch_tail_nb<float, 8>(const TailView<float> &, cudaStream_t);
+template cudaError_t prepare_nb<float, 8>();
+}  // namespace tail
+}  // namespace bm

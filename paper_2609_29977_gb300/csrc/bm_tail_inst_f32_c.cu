@@ -1,0 +1,11 @@
+// Explicit instantiations of the tail factorization kernels (float, nb in [24, 32]).
+#include "bm_tail_factor.cuh"
+
+namespace bm {
+namespace tail {
+template void launch_tail_nb<float, 24>(const TailView<float> &, cudaStream_t);
+template cudaError_t prepare_nb<float, 24>();
+template void launch_tail_nb<float, 32>(const TailView<float> &, cudaStream_t);
+template cudaError_t prepare_nb<float, 32>();
+}  // namespace tail
+}  // namespace bm

@@ -1,0 +1,9 @@
+// Explicit instantiations of the tail factorization kernels (float, nb in [48]).
+#include "bm_tail_factor.cuh"
+
+namespace bm {
+namespace tail {
+template void launch_tail_nb<float, 48>(const TailView<float> &, cudaStream_t);
+template cudaError_t prepare_nb<float, 48>();
+}  // namespace tail
+}  // namespace bm

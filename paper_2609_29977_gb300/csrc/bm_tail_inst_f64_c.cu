@@ -1,0 +1,11 @@
+// Explicit instantiations of the tail factorization kernels (double, nb in [24, 32]).
+#include "bm_tail_factor.cuh"
+
+namespace bm {
+namespace tail {
+template void launch_tail_nb<double, 24>(const TailView<double> &, cudaStream_t);
+template cudaError_t prepare_nb<double, 24>();
+template void launch_tail_nb<double, 32>(const TailView<double> &, cudaStream_t);
+template cudaError_t prepare_nb<double, 32>();
+}  // namespace tail
+}  // namespace bm

@@ -1,0 +1,9 @@
+// Explicit instantiations of the tail factorization kernels (double, nb in [48]).
+#include "bm_tail_factor.cuh"
+
+namespace bm {
+namespace tail {
+template void launch_tail_nb<double, 48>(const TailView<double> &, cudaStream_t);
+template cudaError_t prepare_nb<double, 48>();
+}  // namespace tail
+}  // namespace bm

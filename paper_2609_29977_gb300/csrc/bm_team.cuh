@@ -79,6 +79,66 @@ __device__ __forceinline__ bool pivot_ok<float>(float d) {
   return b > 0 && b < 0x7f800000;
 }
 
+// FP64 -> FP32 rounding to nearest even, done with integer instructions
+// from the IEEE 754 binary64/binary32 encodings (on this GPU the F2F
+// conversion instruction runs on the slow FP64 pipe). Overflow gives inf,
+// results below the FP32 normal range are rounded to subnormals or zero,
+// NaN stays NaN.
+__device__ __forceinline__ float d2f_rn(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ff);
+  unsigned long long m = b & 0x000fffffffffffffull;
+  if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (m ? 0x00400000u : 0u));
+  const int e32 = e - 1023 + 127;
+  if (e32 >= 255) return __uint_as_float(sign | 0x7f800000u);
+  if (e32 <= 0) {
+    const int shift = 1 - e32;
+    if (e == 0 || shift > 24) return __uint_as_float(sign);
+    m |= 1ull << 52;
+    const int sh = 29 + shift;
+    unsigned long long q = m >> sh;
+    const unsigned long long rem = m & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (q & 1ull))) ++q;
+    return __uint_as_float(sign | (unsigned)q);
+  }
+  const unsigned long long rem = m & ((1ull << 29) - 1), half = 1ull << 28;
+  unsigned bits = ((unsigned)e32 << 23) | (unsigned)(m >> 29);
+  if (rem > half || (rem == half && (bits & 1u))) ++bits;
+  return __uint_as_float(sign | bits);
+}
+
+// FP32 -> FP64 (exact), with integer instructions.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned sign = b & 0x80000000u;
+  int e = (int)((b >> 23) & 0xff);
+  unsigned m = b & 0x007fffffu;
+  if (e == 0xff) return __hiloint2double((int)(sign | 0x7ff00000u | (m >> 3)), (int)(m << 29));
+  if (e == 0) {
+    if (m == 0) return __hiloint2double((int)sign, 0);
+    const int lz = __clz(m) - 8;   // bring the leading one to bit 23
+    m = (m << lz) & 0x007fffffu;
+    e = 1 - lz;
+  }
+  const unsigned ed = (unsigned)(e - 127 + 1023);
+  return __hiloint2double((int)(sign | (ed << 20) | (m >> 3)), (int)(m << 29));
+}
+
+template <typename T>
+__device__ __forceinline__ T to_t(double d);
+template <>
+__device__ __forceinline__ double to_t<double>(double d) { return d; }
+template <>
+__device__ __forceinline__ float to_t<float>(double d) { return d2f_rn(d); }
+
+template <typename T>
+__device__ __forceinline__ double to_d(T x);
+template <>
+__device__ __forceinline__ double to_d<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ double to_d<float>(float x) { return f2d_exact(x); }
+
 // Programmatic dependent launch: wait for the preceding kernel's results /
 // let the next kernel start its launch. Both are no-ops without PDL.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
