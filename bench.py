@@ -239,6 +239,9 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     prec = bm.BM_PREC_FP64 if args.precision == "fp64" else bm.BM_PREC_FP32_IR
     w = bmgen.WORKLOADS[args.workload]
+    if args.shape:
+        S_, N_, nb_, nr_ = (int(t) for t in args.shape.split(","))
+        w = w.with_shape(name="%s-shape-%d-%d-%d-%d" % (w.name, S_, N_, nb_, nr_), S=S_, N=N_, nb=nb_, nr=nr_)
     sysd = bmgen.generate(w, instance=rank)
     g = {k: v.to(dev) for k, v in sysd.items() if isinstance(v, torch.Tensor)}
     fl = bmgen.method_flops(w.S, w.N, w.nb, w.nr)
@@ -371,6 +374,7 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--ref-budget", type=float, default=10.0, help="seconds of oracle work")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shape", default="", help="S,N,nb,nr override of the workload's shape (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

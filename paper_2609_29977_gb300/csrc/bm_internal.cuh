@@ -103,6 +103,8 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Block sizes with compile-time tail kernels.
 #define BM_TAIL_NB_LIST(X) X(2) X(3) X(4) X(6) X(8) X(12) X(16) X(24) X(32) X(48)
+// Block sizes whose FP32 tails use the register-row kernels (bm_tail_rows.cuh).
+#define BM_ROWS_NB_LIST(X) X(2) X(3) X(4) X(6) X(8) X(12) X(16) X(24) X(32)
 
 // First level handled by the per-tail top kernel: the first one with at
 // most four positions per tail (Lc when none).

@@ -2,6 +2,7 @@
 // The kernels are defined in bm_tail_factor.cuh and instantiated in
 // bm_tail_inst_*.cu.
 #include "bm_tail_factor.cuh"
+#include "bm_tail_rows.cuh"
 
 namespace bm {
 namespace tail {
@@ -13,6 +14,13 @@ namespace tail {
 BM_TAIL_NB_LIST(X)
 #undef X
 }  // namespace tail
+namespace rows {
+#define X(n)                                                                                  \
+  extern template void launch_tail_rows<float, n>(const TailView<float> &, cudaStream_t); \
+  extern template cudaError_t prepare_rows<float, n>();
+BM_ROWS_NB_LIST(X)
+#undef X
+}  // namespace rows
 
 bool tail_nb_supported(int nb) {
   switch (nb) {
@@ -35,13 +43,28 @@ cudaError_t tail_factor_prepare() {
   if (e == cudaSuccess) e = tail::prepare_nb<float, n>();
   BM_TAIL_NB_LIST(X)
 #undef X
+#define X(n) \
+  if (e == cudaSuccess) e = rows::prepare_rows<float, n>();
+  BM_ROWS_NB_LIST(X)
+#undef X
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
   return e;
 }
 
 // Tail levels and x_1 of the factor (the root step is launched separately).
+// FP32 tails with blocks up to 32 use the register-row kernels.
 template <typename T>
 void tail_factor_launch(const TailView<T> &v, cudaStream_t st) {
+  if (sizeof(T) == 4) {
+    switch (v.nb) {
+#define X(n)                                                                        \
+  case n:                                                                           \
+    rows::launch_tail_rows<float, n>(*reinterpret_cast<const TailView<float> *>(&v), st); \
+    return;
+      BM_ROWS_NB_LIST(X)
+#undef X
+    }
+  }
   switch (v.nb) {
 #define X(n)                           \
   case n:                              \

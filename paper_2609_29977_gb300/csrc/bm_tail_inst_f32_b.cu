@@ -1,5 +1,6 @@
 // Explicit instantiations of the tail factorization kernels (float, nb in [12, 16]).
 #include "bm_tail_factor.cuh"
+#include "bm_tail_rows.cuh"
 
 namespace bm {
 namespace tail {
@@ -8,4 +9,8 @@ template cudaError_t prepare_nb<float, 12>();
 template void launch_tail_nb<float, 16>(const TailView<float> &, cudaStream_t);
 template cudaError_t prepare_nb<float, 16>();
 }  // namespace tail
+template void rows::launch_tail_rows<float, 12>(const TailView<float> &, cudaStream_t);
+template cudaError_t rows::prepare_rows<float, 12>();
+template void rows::launch_tail_rows<float, 16>(const TailView<float> &, cudaStream_t);
+template cudaError_t rows::prepare_rows<float, 16>();
 }  // namespace bm

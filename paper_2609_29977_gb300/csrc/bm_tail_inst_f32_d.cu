@@ -1,5 +1,6 @@
 // Explicit instantiations of the tail factorization kernels (float, nb in [48]).
 #include "bm_tail_factor.cuh"
+#include "bm_tail_rows.cuh"
 
 namespace bm {
 namespace tail {

@@ -1,0 +1,398 @@
+// Register-resident variant of the tail tasks (Alg. 1, steps 1-3) for block
+// sizes up to 32: a team of TS = next power of two >= NB lanes (at most one
+// warp) handles one chain position, lane i holding row i of every block it
+// works on in registers:
+//   * the gathered Schur update D~_q -= X X^T streams the other rows of X
+//     from shared memory (broadcast reads),
+//   * the Cholesky of D~_q is right-looking with each column's entries
+//     exchanged by warp shuffles (no shared memory, no barrier),
+//   * the two coupling solves M L^{-T} reuse the shuffled columns of L,
+//   * the fill -L_{b,q} L_{a,q}^T streams L_{a,q} from shared memory.
+// D~ is kept with both triangles (each lane owns a full row), so the level
+// workspace is read back row by row. Used for the FP32 tails of the mixed
+// path, where the shared-memory variant is latency-bound.
+#pragma once
+
+#include "bm_team.cuh"
+
+namespace bm {
+namespace rows {
+
+template <int NB>
+struct Cfg {
+  static constexpr int TS = NB <= 4 ? 4 : NB <= 8 ? 8 : NB <= 16 ? 16 : 32;
+  static constexpr int LD = NB + 1;   // padded row stride of staged blocks (no bank conflicts)
+  static constexpr int SM = NB * LD;  // staged block size in elements
+};
+
+template <typename T>
+__device__ __forceinline__ T shfl(unsigned mask, T v, int src, int width) {
+  return __shfl_sync(mask, v, src, width);
+}
+
+// Copy an NB x NB block (global, type T) into shared memory with the team
+// (row stride Cfg<NB>::LD).
+template <typename T, int NB, int TS>
+__device__ __forceinline__ void stage(T *__restrict__ s, const T *__restrict__ g, int lane) {
+#pragma unroll
+  for (int e = lane; e < NB * NB; e += TS) {
+    const int r = e / NB, c = e - r * NB;
+    s[r * Cfg<NB>::LD + c] = g[e];
+  }
+}
+
+// d[j] -= sum_k X[i][k] X[j][k] for all j, X staged in sX, row i = lane.
+template <typename T, int NB>
+__device__ __forceinline__ void syrk_row(T (&d)[NB], const T *__restrict__ sX, int ir) {
+  constexpr int LD = Cfg<NB>::LD;
+  T xi[NB];
+#pragma unroll
+  for (int k = 0; k < NB; ++k) xi[k] = sX[ir * LD + k];
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < NB; ++k) acc = fma_t<T>(xi[k], sX[j * LD + k], acc);
+    d[j] -= acc;
+  }
+}
+
+// Right-looking Cholesky on rows held by lanes (lane i has row i in d[]).
+// On return d[j] (j <= i) is L_ij; rinv is 1/L_ii. Returns 1 + the first
+// failing column (uniform over the team), 0 if all pivots are positive.
+template <typename T, int NB, int TS>
+__device__ __forceinline__ int chol_rows(T (&d)[NB], T &rinv, unsigned mask, int i) {
+  int fail = 0;
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    T piv = shfl<T>(mask, d[j], j, TS);
+    if (!pivot_ok(piv)) {
+      if (!fail) fail = j + 1;
+      piv = T(1);
+    }
+    const T r = rsqrt_t<T>(piv);
+    if (i == j) {
+      d[j] = piv * r;
+      rinv = r;
+    } else {
+      d[j] *= r;
+    }
+#pragma unroll
+    for (int k = j + 1; k < NB; ++k) {
+      const T lkj = shfl<T>(mask, d[j], k, TS);
+      d[k] = fma_t<T>(-d[j], lkj, d[k]);
+    }
+  }
+  return fail;
+}
+
+// b := b L^{-T}, a := a L^{-T} for the rows held by this lane; L is
+// distributed by rows over the team (lane k holds L_k* in lk[]).
+template <typename T, int NB, int TS, bool TWO>
+__device__ __forceinline__ void trsm_rows(T (&b)[NB], T (&a)[NB], const T (&lk)[NB], T rinv, unsigned mask) {
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    const T rj = shfl<T>(mask, rinv, j, TS);
+    b[j] *= rj;
+    if (TWO) a[j] *= rj;
+#pragma unroll
+    for (int k = j + 1; k < NB; ++k) {
+      const T lkj = shfl<T>(mask, lk[j], k, TS);
+      b[k] = fma_t<T>(-b[j], lkj, b[k]);
+      if (TWO) a[k] = fma_t<T>(-a[j], lkj, a[k]);
+    }
+  }
+}
+
+// One task of level lvl with register-resident rows.
+template <typename T, int NB>
+__device__ __forceinline__ void factor_task_rows(const TailView<T> &v, T *sX, int lane, unsigned mask, int s, int q,
+                                                 int lvl, bool elim) {
+  constexpr int TS = Cfg<NB>::TS, NB2 = NB * NB;
+  const int N = v.N;
+  const size_t sb = (size_t)s * N;
+  const int i = lane;
+  const bool act = i < NB;
+  const int ir = act ? i : 0;
+  T d[NB];
+  if (lvl <= 1) {
+    const double *Dq = v.D + (sb + (N - q)) * NB2;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) d[j] = to_t<T>(j <= ir ? Dq[ir * NB + j] : Dq[j * NB + ir]);
+  } else {
+    const T *Dq = v.Dt + (sb + (N - q)) * NB2 + ir * NB;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) d[j] = Dq[j];
+  }
+  if (lvl >= 1) {
+    const int h = 1 << (lvl - 1);
+    int pl = 0, pr = 0;
+    if (q < N) {
+      pl = q - h;
+      if (q + h <= N - 1) pr = q + h;
+    } else {
+      const int m = ((N - 1) >> (lvl - 1)) << (lvl - 1);
+      if (ctz32(m) == lvl - 1) pl = m;
+    }
+    if (pl) {
+      stage<T, NB, TS>(sX, v.Lr + (sb + (N - pl)) * NB2, lane);
+      __syncwarp(mask);
+      syrk_row<T, NB>(d, sX, ir);
+      __syncwarp(mask);
+    }
+    if (pr) {
+      stage<T, NB, TS>(sX, v.Ll + (sb + (N - pr)) * NB2, lane);
+      __syncwarp(mask);
+      syrk_row<T, NB>(d, sX, ir);
+      __syncwarp(mask);
+    }
+  }
+  if (!elim) {
+    if (act) {
+      T *o = v.Dt + (sb + (N - q)) * NB2 + i * NB;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) o[j] = d[j];
+    }
+    return;
+  }
+  // couplings: rows i of M_{b,q} and M_{a,q}
+  const int hh = 1 << lvl;
+  const bool hasA = q > hh;
+  const int a = q - hh;
+  T b[NB], av[NB];
+  if (lvl == 0 || q == N - 1) {
+    const double *Eb = v.E + ((size_t)s * (N - 1) + (N - q - 1)) * NB2;   // M_{b,q} = E^T
+#pragma unroll
+    for (int k = 0; k < NB; ++k) b[k] = to_t<T>(Eb[k * NB + ir]);
+  } else {
+    const T *Wb = v.W + (sb + (N - q)) * NB2 + ir * NB;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) b[k] = Wb[k];
+  }
+  if (hasA) {
+    if (lvl == 0) {
+      const double *Ea = v.E + ((size_t)s * (N - 1) + (N - q)) * NB2 + ir * NB;
+#pragma unroll
+      for (int k = 0; k < NB; ++k) av[k] = to_t<T>(Ea[k]);
+    } else {
+      const T *Wa = v.W + (sb + (N - a)) * NB2;   // M_{a,q} = W[a]^T
+#pragma unroll
+      for (int k = 0; k < NB; ++k) av[k] = Wa[k * NB + ir];
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < NB; ++k) av[k] = T(0);
+  }
+  T rinv = T(1);
+  const int fail = chol_rows<T, NB, TS>(d, rinv, mask, i);
+  if (i == 0 && fail) report_not_spd(v.status, s, N + 1 - q);
+  if (hasA)
+    trsm_rows<T, NB, TS, true>(b, av, d, rinv, mask);
+  else
+    trsm_rows<T, NB, TS, false>(b, av, d, rinv, mask);
+  if (act) {
+    T *Ld = v.Ld + (sb + (N - q)) * NB2 + i * NB;
+    T *Lb = v.Lr + (sb + (N - q)) * NB2 + i * NB;
+    T *La = v.Ll + (sb + (N - q)) * NB2 + i * NB;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      Ld[j] = j <= i ? d[j] : T(0);
+      Lb[j] = b[j];
+      La[j] = av[j];
+    }
+    v.invd[(sb + (N - q)) * NB + i] = rinv;
+  }
+  if (hasA) {
+    // fill M_{b,a} = -L_{b,q} L_{a,q}^T: stage the rows of L_{a,q}
+    constexpr int LD = Cfg<NB>::LD;
+    if (act) {
+#pragma unroll
+      for (int k = 0; k < NB; ++k) sX[i * LD + k] = av[k];
+    }
+    __syncwarp(mask);
+    if (act) {
+      T *Wo = v.W + (sb + (N - a)) * NB2 + i * NB;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        T acc = T(0);
+#pragma unroll
+        for (int k = 0; k < NB; ++k) acc = fma_t<T>(b[k], sX[j * LD + k], acc);
+        Wo[j] = -acc;
+      }
+    }
+    __syncwarp(mask);
+  }
+}
+
+// x_1 of tail s: last update and L_{i,1} with register rows, then F_{i,1} =
+// C_{i,1} L_{i,1}^{-T} and U_i = F F^T in FP64. sbuf: nr*NB doubles followed
+// by NB*NB + NB values of type T.
+template <typename T, int NB>
+__device__ __forceinline__ void x1_task_rows(const TailView<T> &v, void *sbuf, int lane, unsigned mask, int s) {
+  constexpr int TS = Cfg<NB>::TS, NB2 = NB * NB;
+  const int N = v.N, nr = v.nr, Lc = v.Lc;
+  const size_t sb = (size_t)s * N;
+  constexpr int LD = Cfg<NB>::LD;
+  double *sC = (double *)sbuf;
+  T *sL = (T *)(sC + nr * NB), *sInv = sL + NB * LD;
+  const int i = lane;
+  const bool act = i < NB;
+  const int ir = act ? i : 0;
+  T d[NB];
+  if (Lc <= 1) {
+    const double *Dq = v.D + sb * NB2;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) d[j] = to_t<T>(j <= ir ? Dq[ir * NB + j] : Dq[j * NB + ir]);
+  } else {
+    const T *Dq = v.Dt + sb * NB2 + ir * NB;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) d[j] = Dq[j];
+  }
+  if (Lc >= 1) {
+    const int m = 1 << (Lc - 1);
+    stage<T, NB, TS>(sL, v.Lr + (sb + (N - m)) * NB2, lane);
+    __syncwarp(mask);
+    syrk_row<T, NB>(d, sL, ir);
+    __syncwarp(mask);
+  }
+  T rinv = T(1);
+  const int fail = chol_rows<T, NB, TS>(d, rinv, mask, i);
+  if (i == 0 && fail) report_not_spd(v.status, s, 1);
+  if (act) {
+    T *Ld = v.Ld + sb * NB2 + i * NB;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      Ld[j] = j <= i ? d[j] : T(0);
+      sL[i * LD + j] = j <= i ? d[j] : T(0);
+      v.Lr[sb * NB2 + i * NB + j] = T(0);
+      v.Ll[sb * NB2 + i * NB + j] = T(0);
+    }
+    v.invd[sb * NB + i] = rinv;
+    sInv[i] = rinv;
+  }
+  for (int e = lane; e < nr * NB; e += TS) sC[e] = v.C[(size_t)s * nr * NB + e];
+  __syncwarp(mask);
+  // F = C L^{-T} in FP64, one row of C per lane (column sweep within the row)
+  for (int c = lane; c < nr; c += TS) {
+    double f[NB];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) f[k] = sC[c * NB + k];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      f[j] *= to_d<T>(sInv[j]);
+#pragma unroll
+      for (int k = j + 1; k < NB; ++k) f[k] = fma(-f[j], to_d<T>(sL[k * LD + j]), f[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+      sC[c * NB + k] = f[k];
+      v.F[(size_t)s * nr * NB + c * NB + k] = f[k];
+    }
+  }
+  __syncwarp(mask);
+  double *Us = v.U + (size_t)s * nr * nr;
+  for (int e = lane; e < nr * nr; e += TS) {
+    const int a = e / nr, b = e - a * nr;
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) acc = fma(sC[a * NB + k], sC[b * NB + k], acc);
+    Us[e] = acc;
+  }
+}
+
+template <typename T, int NB>
+__host__ __device__ constexpr size_t x1_rows_bytes(int nr) {
+  return (size_t)nr * NB * sizeof(double) + (NB * (NB + 1) + NB) * sizeof(T);
+}
+
+}  // namespace rows
+}  // namespace bm
+
+namespace bm {
+namespace rows {
+
+// Grid-wide level with register rows: tasks of all tails, eliminated
+// positions first; TS lanes per task, 128 threads per CTA.
+template <typename T, int NB>
+__global__ void __launch_bounds__(128) k_level_rows(TailView<T> v, int lvl) {
+  constexpr int TS = Cfg<NB>::TS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int team = threadIdx.x / TS, lane = threadIdx.x % TS;
+  const unsigned mask = TS == 32 ? 0xffffffffu : (((1u << TS) - 1u) << ((threadIdx.x & 31) / TS * TS));
+  T *sX = (T *)smem_raw + team * Cfg<NB>::SM;
+  const int N = v.N, S = v.S;
+  const int E = level_elims(N, lvl);
+  const int G = lvl == 0 ? 0 : ((N - 1) >> (lvl + 1)) + 1;
+  const long g = (long)blockIdx.x * (blockDim.x / TS) + team;
+  pdl_wait();
+  if (g < (long)S * (E + G)) {
+    int s, q;
+    bool elim;
+    if (g < (long)S * E) {
+      s = (int)(g / E);
+      q = (2 * (int)(g - (long)s * E) + 1) << lvl;
+      elim = true;
+    } else {
+      const long g2 = g - (long)S * E;
+      s = (int)(g2 / G);
+      const int j = (int)(g2 - (long)s * G);
+      q = j < G - 1 ? (j + 1) << (lvl + 1) : N;
+      elim = false;
+    }
+    factor_task_rows<T, NB>(v, sX, lane, mask, s, q, lvl, elim);
+  }
+  pdl_trigger();
+}
+
+// Top levels lvl0..Lc-1 and x_1 of one tail per CTA (four teams).
+template <typename T, int NB>
+__global__ void __launch_bounds__(128) k_top_rows(TailView<T> v, int lvl0) {
+  constexpr int TS = Cfg<NB>::TS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int team = threadIdx.x / TS, lane = threadIdx.x % TS, teams = blockDim.x / TS;
+  const unsigned mask = TS == 32 ? 0xffffffffu : (((1u << TS) - 1u) << ((threadIdx.x & 31) / TS * TS));
+  T *sX = (T *)smem_raw + team * Cfg<NB>::SM;
+  const int N = v.N, s = blockIdx.x;
+  pdl_wait();
+  for (int lvl = lvl0; lvl < v.Lc; ++lvl) {
+    const int E = level_elims(N, lvl);
+    const int G = lvl == 0 ? 0 : ((N - 1) >> (lvl + 1)) + 1;
+    for (int t = team; t < E + G; t += teams) {
+      const bool elim = t < E;
+      const int q = elim ? (2 * t + 1) << lvl : (t - E < G - 1 ? (t - E + 1) << (lvl + 1) : N);
+      factor_task_rows<T, NB>(v, sX, lane, mask, s, q, lvl, elim);
+    }
+    __syncthreads();
+  }
+  if (team == 0) x1_task_rows<T, NB>(v, smem_raw, lane, mask, s);
+  pdl_trigger();
+}
+
+template <typename T, int NB>
+cudaError_t prepare_rows() {
+  cudaError_t e = cudaFuncSetAttribute(k_level_rows<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_top_rows<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+}
+
+template <typename T, int NB>
+void launch_tail_rows(const TailView<T> &v, cudaStream_t st) {
+  constexpr int TS = Cfg<NB>::TS;
+  const int Tl = top_level(v.N);
+  const int tpc = 128 / TS;
+  for (int l = 0; l < Tl; ++l) {
+    const int E = level_elims(v.N, l);
+    const int G = l == 0 ? 0 : ((v.N - 1) >> (l + 1)) + 1;
+    const long tasks = (long)v.S * (E + G);
+    const long blocks = (tasks + tpc - 1) / tpc;
+    launch_pdl(k_level_rows<T, NB>, (unsigned)blocks, 128, (size_t)tpc * Cfg<NB>::SM * sizeof(T), st, v, l);
+  }
+  const int teams = 4;
+  size_t smem = (size_t)teams * Cfg<NB>::SM * sizeof(T);
+  const size_t x1b = x1_rows_bytes<T, NB>(v.nr);
+  if (x1b > smem) smem = x1b;
+  launch_pdl(k_top_rows<T, NB>, (unsigned)v.S, teams * TS, smem, st, v, Tl);
+}
+
+}  // namespace rows
+}  // namespace bm

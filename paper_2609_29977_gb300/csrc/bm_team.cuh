@@ -84,7 +84,7 @@ __device__ __forceinline__ bool pivot_ok<float>(float d) {
 // conversion instruction runs on the slow FP64 pipe). Overflow gives inf,
 // results below the FP32 normal range are rounded to subnormals or zero,
 // NaN stays NaN.
-__device__ __forceinline__ float d2f_rn(double d) {
+__device__ __forceinline__ float d2f_rn_slow(double d) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(d);
   const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
   const int e = (int)((b >> 52) & 0x7ff);
@@ -106,6 +106,20 @@ __device__ __forceinline__ float d2f_rn(double d) {
   unsigned bits = ((unsigned)e32 << 23) | (unsigned)(m >> 29);
   if (rem > half || (rem == half && (bits & 1u))) ++bits;
   return __uint_as_float(sign | bits);
+}
+
+// Fast path with 32-bit integer instructions for results in the FP32 normal
+// range (binary64 exponent 897..1150); everything else goes to d2f_rn_slow.
+__device__ __forceinline__ float d2f_rn(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  if (e - 897u < 253u) {
+    unsigned bits = (hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0x000fffffu) << 3) | (lo >> 29);
+    const unsigned rem = lo & 0x1fffffffu;
+    bits += (rem > 0x10000000u) | ((rem == 0x10000000u) & bits);
+    return __uint_as_float(bits);
+  }
+  return d2f_rn_slow(d);
 }
 
 // FP32 -> FP64 (exact), with integer instructions.
