@@ -222,6 +222,101 @@ def run_reference(args):
     return 0
 
 
+def run_batched(args):
+    """The batched workload: 256 systems with S~U{8..256}, N~U{16..256},
+    nb in {6,12,24,48}, nr = ceil(nb/3), barrier 10^U[-4,4], factored in one
+    persistent launch and solved with FP32 tails + FP64 refinement. One step
+    = bm_batch_factor + bm_batch_solve of the whole batch. Beside it, the
+    same systems through the plain FP64 path, one handle per system."""
+    import torch
+
+    import bmgen
+    import paper_2609_29977_gb300 as bm
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    count = args.batch_count
+    shapes = bmgen.draw_batched_shapes(count)
+    base = bmgen.Workload("batched", 1, 1, 1, 1, workload_id=4, barrier=(-4.0, 4.0), shared_A=True)
+    t0 = time.perf_counter()
+    systems = []
+    for j, (S, N, nb, nr) in enumerate(shapes):
+        systems.append(bmgen.generate(base.with_shape(S=S, N=N, nb=nb, nr=nr), instance=j, device=dev))
+    gen_s = time.perf_counter() - t0
+    flops = sum(bmgen.method_flops(S, N, nb, nr)["total"] for (S, N, nb, nr) in shapes)
+    batch = bm.BranchKKTBatch(shapes, max_refine=args.max_refine, tol=args.tol)
+    Ds, Es, Cs, Rs, rs = ([d[k] for d in systems] for k in ("D", "E", "C", "R", "r"))
+    xs = [torch.empty_like(r) for r in rs]
+    t0 = time.perf_counter()
+    batch.factor(Ds, Es, Cs, Rs)     # first call autotunes the persistent launch
+    torch.cuda.synchronize()
+    tune_s = time.perf_counter() - t0
+    for _ in range(max(3, args.warmup)):
+        batch.factor(Ds, Es, Cs, Rs)
+        batch.solve(rs, xs)
+    infos = batch.query()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler("0")
+    sampler.start()
+    time.sleep(0.5)
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        a, b, c = ev[i]
+        a.record(stream)
+        batch.factor(Ds, Es, Cs, Rs)
+        b.record(stream)
+        batch.solve(rs, xs)
+        c.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    fac = statistics.mean(a.elapsed_time(b) for a, b, _ in ev)
+    sol = statistics.mean(b.elapsed_time(c) for _, b, c in ev)
+    infos = batch.query()
+    etas = [i["backward_error"] for i in infos]
+    bad = [i for i in infos if i["status"] != 0]
+    sched = batch.schedule()
+    batch.close()
+    # the plain FP64 path on the same systems, one handle per system, back to back
+    fp64_ms = None
+    if not args.no_fp64_compare:
+        # one system at a time (a handle per system would not fit beside the
+        # batch): factor + solve timed with events after a warm-up, summed
+        fp64_ms = 0.0
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for (S, N, nb, nr), d in zip(shapes, systems):
+            hnd = bm.BranchKKTSolver(S, N, nb, nr)
+            x64 = torch.empty_like(d["r"])
+            hnd.factor(d["D"], d["E"], d["C"], d["R"])
+            hnd.solve(d["r"], x64)
+            flush.zero_()
+            a.record(stream)
+            hnd.factor(d["D"], d["E"], d["C"], d["R"])
+            hnd.solve(d["r"], x64)
+            b.record(stream)
+            torch.cuda.synchronize()
+            fp64_ms += a.elapsed_time(b)
+            hnd.close()
+            del x64
+    ms = fac + sol
+    line = {
+        "metric": METRIC, "value": flops / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (seeded MPC-shaped generator)",
+        "config": {"workload": "batched-%d" % count, "systems": count, "stages": sum(S * N for S, N, _, _ in shapes),
+                   "precision": "fp32ir", "tol": args.tol, "l2": "flushed between timed steps"},
+        "factor_ms": fac, "solve_ms": sol, "fp64_sequential_ms": fp64_ms,
+        "speedup_vs_fp64_sequential": (fp64_ms / ms) if fp64_ms else None,
+        "backward_error_max": max(etas), "failed_systems": len(bad), "schedule": sched,
+        "autotune_s": tune_s, "generate_s": gen_s, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_gpu(args):
     import torch
 
@@ -375,9 +470,13 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=10.0, help="seconds of oracle work")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shape", default="", help="S,N,nb,nr override of the workload's shape (profiling)")
+    ap.add_argument("--batch-count", type=int, default=256, help="systems in the batched workload")
+    ap.add_argument("--no-fp64-compare", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload.startswith("batched"):
+        return run_batched(args)
     return run_gpu(args)
 
 

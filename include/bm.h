@@ -215,6 +215,60 @@ bm_status bm_factor_solve_noalloc(int S, int N, int nb, int nr, const double *D,
  */
 bm_status bm_round_to_fp32(const double *src, float *dst, size_t n, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched form: many independent systems of uneven S, N, nb (and nr) in one
+ * object, solved with the mixed-precision method (FP32 tails, FP64 root,
+ * FP64 iterative refinement). Not in the paper; every system is the one of
+ * Sec. III-B and is factored and solved as in bm_factor / bm_solve.
+ * ------------------------------------------------------------------------- */
+typedef struct bm_batch_s *bm_batch;
+
+/* Device bytes bm_batch_analyze allocates, or 0 if a desc is invalid
+ * (precision must be BM_PREC_FP32_IR; nb in {4, 6, 12, 24, 48};
+ * nr <= 64; S <= 65535). */
+size_t bm_batch_workspace_bytes(const bm_desc *descs, int count);
+
+/*
+ * One-time analysis of a batch of count systems: builds the work queues of
+ * the persistent factor launch (one per block size, items ordered by the
+ * odd-even levels of Gamma_{N-1}, Sec. II) and allocates all factors and
+ * workspaces. max_refine and tol are taken from descs[0].
+ * Errors: BM_ERR_INVALID_ARG, BM_ERR_OOM, BM_ERR_CUDA.
+ */
+bm_status bm_batch_analyze(const bm_desc *descs, int count, void *stream, bm_batch *out);
+
+/*
+ * Factors every system of the batch (Alg. 1) in one persistent launch.
+ * D, E, C, R are DEVICE arrays of count device pointers (layouts as for
+ * bm_factor; E[b] may be NULL when N_b = 1); the pointed-to inputs must stay
+ * valid until the next bm_batch_factor (the refinement reads them). The
+ * first call on a handle autotunes the launch shape (threads per CTA, CTAs
+ * per SM) by timing candidates on these inputs, synchronizing the stream,
+ * unless a cached choice for the same batch signature and GPU exists
+ * (cache file: $BM_AUTOTUNE_CACHE, else ~/.cache/branch_mpc_gb300_autotune.json).
+ * Asynchronous afterwards. Device failures go to each system's status.
+ */
+bm_status bm_batch_factor(bm_batch b, const double *const *D, const double *const *E, const double *const *C,
+                          const double *const *R, void *stream);
+
+/*
+ * Solves every system (Alg. 2 with FP32 tails and an FP64 root step, then
+ * FP64 refinement until each system's backward error <= tol); r and x are
+ * DEVICE arrays of count device pointers. Asynchronous.
+ */
+bm_status bm_batch_solve(bm_batch b, const double *const *r, double *const *x, void *stream);
+
+/* Synchronizes stream; fills infos[count] (may be NULL); returns the first
+ * non-OK system status, or BM_OK. */
+bm_status bm_batch_query(bm_batch b, void *stream, bm_info *infos);
+
+/* The launch shape chosen by the autotuner (BM_ERR_NOT_FACTORED before the
+ * first bm_batch_factor); *from_cache = 1 when it came from the cache. */
+bm_status bm_batch_schedule(bm_batch b, int *threads_per_cta, int *ctas_per_sm, int *from_cache);
+
+/* Frees everything the batch owns. */
+void bm_batch_destroy(bm_batch b);
+
 /* Frees everything the handle owns (synchronizes its internal stream). */
 void bm_destroy(bm_handle h);
 

@@ -6,11 +6,14 @@ The compute runs in the CUDA library ``libbm.so`` (C ABI in include/bm.h);
 package does not load the library; the first call does, and raises if the
 library was not built (``python -c "import __graft_entry__ as g; g.build()"``).
 """
+from .bm import (BATCH_NB, BranchKKTBatch, bm_batch_analyze, bm_batch_destroy, bm_batch_factor, bm_batch_query,
+                 bm_batch_schedule, bm_batch_solve, bm_batch_workspace_bytes)
 from .bm import (BM_FLAG_NO_GRAPH, BM_PREC_FP32_IR, BM_PREC_FP64, BMError, BranchKKTSolver, bm_analyze,
                  bm_destroy, bm_export_factor, bm_factor, bm_factor_solve_host, bm_factor_solve_noalloc, bm_query, bm_round_to_fp32, bm_solve,
                  bm_status_string, bm_version, bm_workspace_bytes, library_path)
 
-__all__ = ["BranchKKTSolver", "BMError", "bm_analyze", "bm_factor", "bm_solve", "bm_query",
+__all__ = ["BranchKKTBatch", "BATCH_NB", "bm_batch_analyze", "bm_batch_factor", "bm_batch_solve", "bm_batch_query",
+           "bm_batch_schedule", "bm_batch_destroy", "bm_batch_workspace_bytes", "BranchKKTSolver", "BMError", "bm_analyze", "bm_factor", "bm_solve", "bm_query",
            "bm_export_factor", "bm_factor_solve_host", "bm_factor_solve_noalloc", "bm_round_to_fp32", "bm_destroy", "bm_workspace_bytes",
            "bm_version", "bm_status_string", "library_path", "BM_PREC_FP64", "BM_PREC_FP32_IR",
            "BM_FLAG_NO_GRAPH"]

@@ -24,7 +24,10 @@ STATUS_NAMES = {0: "BM_OK", 1: "BM_ERR_INVALID_ARG", 2: "BM_ERR_NOT_SPD", 3: "BM
 
 EXPORTED_SYMBOLS = ("bm_version", "bm_status_string", "bm_workspace_bytes", "bm_analyze", "bm_factor",
                     "bm_solve", "bm_query", "bm_export_factor", "bm_factor_solve_host", "bm_destroy",
-                    "bm_factor_solve_noalloc", "bm_round_to_fp32")
+                    "bm_factor_solve_noalloc", "bm_round_to_fp32", "bm_batch_workspace_bytes",
+                    "bm_batch_analyze", "bm_batch_factor", "bm_batch_solve", "bm_batch_query",
+                    "bm_batch_schedule", "bm_batch_destroy")
+BATCH_NB = (4, 6, 12, 24, 48)
 BM_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -81,6 +84,21 @@ def _load():
     lib.bm_factor_solve_host.argtypes = [vp, dp, dp, dp, dp, dp, dp, vp]
     lib.bm_destroy.restype = None
     lib.bm_destroy.argtypes = [vp]
+    lib.bm_batch_workspace_bytes.restype = sz
+    lib.bm_batch_workspace_bytes.argtypes = [ctypes.POINTER(bm_desc), ctypes.c_int]
+    lib.bm_batch_analyze.restype = ctypes.c_int
+    lib.bm_batch_analyze.argtypes = [ctypes.POINTER(bm_desc), ctypes.c_int, vp, ctypes.POINTER(vp)]
+    lib.bm_batch_factor.restype = ctypes.c_int
+    lib.bm_batch_factor.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.bm_batch_solve.restype = ctypes.c_int
+    lib.bm_batch_solve.argtypes = [vp, vp, vp, vp]
+    lib.bm_batch_query.restype = ctypes.c_int
+    lib.bm_batch_query.argtypes = [vp, vp, ctypes.POINTER(bm_info)]
+    lib.bm_batch_schedule.restype = ctypes.c_int
+    lib.bm_batch_schedule.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int)]
+    lib.bm_batch_destroy.restype = None
+    lib.bm_batch_destroy.argtypes = [vp]
     lib.bm_round_to_fp32.restype = ctypes.c_int
     lib.bm_round_to_fp32.argtypes = [dp, dp, ctypes.c_size_t, vp]
     lib.bm_factor_solve_noalloc.restype = ctypes.c_int
@@ -257,6 +275,111 @@ class BranchKKTSolver:
     def close(self):
         if self.h:
             bm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- batched form ---------------------------------------------------------------
+
+def _desc_array(shapes, max_refine, tol):
+    arr = (bm_desc * len(shapes))()
+    for i, (S, N, nb, nr) in enumerate(shapes):
+        arr[i] = make_desc(S, N, nb, nr, BM_PREC_FP32_IR, max_refine, tol)
+    return arr
+
+
+def bm_batch_workspace_bytes(shapes, max_refine=10, tol=1e-10) -> int:
+    arr = _desc_array(shapes, max_refine, tol)
+    return int(_load().bm_batch_workspace_bytes(arr, len(shapes)))
+
+
+def bm_batch_analyze(shapes, max_refine=10, tol=1e-10, stream=None):
+    arr = _desc_array(shapes, max_refine, tol)
+    h = ctypes.c_void_p()
+    _check(_load().bm_batch_analyze(arr, len(shapes), _stream(stream), ctypes.byref(h)), "bm_batch_analyze")
+    return h
+
+
+def _ptr_array(tensors, name, allow_empty=False):
+    import torch
+    ptrs = []
+    for t in tensors:
+        if t is None or (allow_empty and t.numel() == 0):
+            ptrs.append(0)
+        else:
+            ptrs.append(_ptr(t, name).value)
+    return torch.tensor(ptrs, dtype=torch.int64, device="cuda")
+
+
+def bm_batch_factor(h, Dp, Ep, Cp, Rp, stream=None) -> None:
+    """Dp, Ep, Cp, Rp: int64 CUDA tensors holding the device pointers."""
+    _check(_load().bm_batch_factor(h, ctypes.c_void_p(Dp.data_ptr()), ctypes.c_void_p(Ep.data_ptr()),
+                                   ctypes.c_void_p(Cp.data_ptr()), ctypes.c_void_p(Rp.data_ptr()),
+                                   _stream(stream)), "bm_batch_factor")
+
+
+def bm_batch_solve(h, rp, xp, stream=None) -> None:
+    _check(_load().bm_batch_solve(h, ctypes.c_void_p(rp.data_ptr()), ctypes.c_void_p(xp.data_ptr()),
+                                  _stream(stream)), "bm_batch_solve")
+
+
+def bm_batch_query(h, count, stream=None) -> list:
+    infos = (bm_info * count)()
+    _load().bm_batch_query(h, _stream(stream), infos)
+    return [{"status": i.status, "name": STATUS_NAMES.get(i.status, str(i.status)), "fail_scenario": i.fail_scenario,
+             "fail_stage": i.fail_stage, "iters": i.iters, "backward_error": i.backward_error} for i in infos]
+
+
+def bm_batch_schedule(h) -> dict:
+    t, c, f = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    code = _load().bm_batch_schedule(h, ctypes.byref(t), ctypes.byref(c), ctypes.byref(f))
+    return {"status": code, "threads_per_cta": t.value, "ctas_per_sm": c.value, "from_cache": bool(f.value)}
+
+
+def bm_batch_destroy(h) -> None:
+    if h:
+        _load().bm_batch_destroy(h)
+
+
+class BranchKKTBatch:
+    """Many independent systems (list of (S, N, nb, nr)) factored in one
+    persistent launch and solved with FP32 tails + FP64 refinement."""
+
+    def __init__(self, shapes, max_refine=10, tol=1e-10, stream=None):
+        self.shapes = [tuple(int(v) for v in sh) for sh in shapes]
+        self.count = len(self.shapes)
+        self.h = bm_batch_analyze(self.shapes, max_refine, tol, stream)
+        self._keep = []
+
+    def factor(self, Ds, Es, Cs, Rs, stream=None):
+        arrs = (_ptr_array(Ds, "D"), _ptr_array(Es, "E", True), _ptr_array(Cs, "C"), _ptr_array(Rs, "R"))
+        self._keep = [arrs, list(Ds), list(Es), list(Cs), list(Rs)]
+        bm_batch_factor(self.h, *arrs, stream=stream)
+        return self
+
+    def solve(self, rs, xs=None, stream=None):
+        import torch
+        if xs is None:
+            xs = [torch.empty_like(r) for r in rs]
+        rp, xp = _ptr_array(rs, "r"), _ptr_array(xs, "x")
+        self._keep_solve = [rp, xp, list(rs), list(xs)]
+        bm_batch_solve(self.h, rp, xp, stream)
+        return xs
+
+    def query(self, stream=None) -> list:
+        return bm_batch_query(self.h, self.count, stream)
+
+    def schedule(self) -> dict:
+        return bm_batch_schedule(self.h)
+
+    def close(self):
+        if self.h:
+            bm_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -249,30 +249,29 @@ __global__ void k_factor_x1(F64View v) {
   }
 }
 
-// Root: R~ = R - sum_i U_i (one CTA per lower-triangle element, fixed
-// summation order), then L_R = chol(R~) by the last CTA to finish.
+// Root: R~ = R - sum_i U_i (one thread per lower-triangle entry, fixed
+// summation order root_sum), then L_R = chol(R~) by the last CTA to finish
+// (Alg. 1, steps 4-5).
 __global__ void k_factor_root(F64View v) {
   extern __shared__ double sm[];
-  __shared__ double red[256];
   __shared__ int sflag, last;
-  const int nr = v.nr, S = v.S;
-  int i, j;
-  tri_ij(blockIdx.x, i, j);
-  double acc = 0.0;
-  for (int s = threadIdx.x; s < S; s += blockDim.x) acc += v.U[(size_t)s * nr * nr + i * nr + j];
-  const double tot = cta_sum(acc, red);
-  if (threadIdx.x == 0) {
-    const double val = v.R[i * nr + j] - tot;
+  const int nr = v.nr, ne = nr * (nr + 1) / 2;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < ne) {
+    int i, j;
+    tri_ij(e, i, j);
+    const double val = v.R[i * nr + j] - root_sum(v.U, v.S, nr, i, j);
     v.Rt[i * nr + j] = val;
     v.Rt[j * nr + i] = val;
-    __threadfence();
-    last = (atomicAdd(&v.tickets[0], 1u) == gridDim.x - 1);
   }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(&v.tickets[0], 1u) == gridDim.x - 1);
   __syncthreads();
   if (!last) return;
   __threadfence();
   double *sR = sm, *sInv = sm + nr * nr;
-  for (int e = threadIdx.x; e < nr * nr; e += blockDim.x) sR[e] = __ldcg(v.Rt + e);
+  for (int k = threadIdx.x; k < nr * nr; k += blockDim.x) sR[k] = __ldcg(v.Rt + k);
   __syncthreads();
   if (cta_chol(sR, sInv, nr, &sflag) && threadIdx.x == 0) report_not_spd(v.status, -1, 0);
   cta_store_lower(v.LR, sR, nr);
@@ -517,7 +516,7 @@ void f64_launch_factor(const F64View &v, cudaStream_t st) {
     k_factor_x1<<<v.S, T, smem, st>>>(v);
   }
   const int ne = v.nr * (v.nr + 1) / 2;
-  k_factor_root<<<ne, 256, ((size_t)v.nr * v.nr + v.nr) * sizeof(double), st>>>(v);
+  k_factor_root<<<(ne + 255) / 256, 256, ((size_t)v.nr * v.nr + v.nr) * sizeof(double), st>>>(v);
 }
 
 // Root step of the factor for callers that hold raw buffers (mixed path).
@@ -533,7 +532,7 @@ void f64_launch_factor_root_raw(int S, int nr, const double *U, const double *R,
   v.tickets = tickets;
   v.status = status;
   const int ne = nr * (nr + 1) / 2;
-  k_factor_root<<<ne, 256, ((size_t)nr * nr + nr) * sizeof(double), st>>>(v);
+  k_factor_root<<<(ne + 255) / 256, 256, ((size_t)nr * nr + nr) * sizeof(double), st>>>(v);
 }
 
 void f64_launch_solve_root(const F64View &v, const double *r, double *x, double *r0t, cudaStream_t st) {

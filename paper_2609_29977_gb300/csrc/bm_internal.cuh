@@ -69,6 +69,22 @@ __device__ inline void report_not_spd(Status *st, int scenario, int stage) {
   }
 }
 
+// Root reduction of Alg. 1 step 4 for one entry (i, j): sum_s U_s[i][j] in
+// the library's fixed order -- four accumulators over s = k mod 4, each in
+// increasing s, combined as (a0 + a1) + (a2 + a3) -- so that every code path
+// (single system, batch) gets the same bits for the same system.
+__device__ inline double root_sum(const double *U, int S, int nr, int i, int j) {
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  const size_t stride = (size_t)nr * nr, off = (size_t)i * nr + j;
+  int s = 0;
+  for (; s + 4 <= S; s += 4) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a[k] += U[(size_t)(s + k) * stride + off];
+  }
+  for (int k = 0; s < S; ++s, ++k) a[k] += U[(size_t)s * stride + off];
+  return (a[0] + a[1]) + (a[2] + a[3]);
+}
+
 // Views passed to the FP64 kernels (by value).
 struct F64View {
   int S, N, nb, nr, Lc;

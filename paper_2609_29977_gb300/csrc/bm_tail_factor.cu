@@ -20,6 +20,8 @@ namespace rows {
   extern template cudaError_t prepare_rows<float, n>();
 BM_ROWS_NB_LIST(X)
 #undef X
+extern template void launch_tail_rows_w<float, 48>(const TailView<float> &, cudaStream_t);
+extern template cudaError_t prepare_rows_w<float, 48>();
 }  // namespace rows
 
 bool tail_nb_supported(int nb) {
@@ -47,12 +49,13 @@ cudaError_t tail_factor_prepare() {
   if (e == cudaSuccess) e = rows::prepare_rows<float, n>();
   BM_ROWS_NB_LIST(X)
 #undef X
+  if (e == cudaSuccess) e = rows::prepare_rows_w<float, 48>();
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
   return e;
 }
 
 // Tail levels and x_1 of the factor (the root step is launched separately).
-// FP32 tails with blocks up to 32 use the register-row kernels.
+// FP32 tails use the register-row kernels (two-warp teams for nb = 48).
 template <typename T>
 void tail_factor_launch(const TailView<T> &v, cudaStream_t st) {
   if (sizeof(T) == 4) {
@@ -63,6 +66,9 @@ void tail_factor_launch(const TailView<T> &v, cudaStream_t st) {
     return;
       BM_ROWS_NB_LIST(X)
 #undef X
+      case 48:
+        rows::launch_tail_rows_w<float, 48>(*reinterpret_cast<const TailView<float> *>(&v), st);
+        return;
     }
   }
   switch (v.nb) {

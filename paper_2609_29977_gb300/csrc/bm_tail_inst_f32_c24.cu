@@ -1,4 +1,4 @@
-// Explicit instantiations of the tail factorization kernels (float, nb in [24, 32]).
+// Explicit instantiations of the tail factorization kernels (float, nb = 24).
 #include "bm_tail_factor.cuh"
 #include "bm_tail_rows.cuh"
 
@@ -6,11 +6,7 @@ namespace bm {
 namespace tail {
 template void launch_tail_nb<float, 24>(const TailView<float> &, cudaStream_t);
 template cudaError_t prepare_nb<float, 24>();
-template void launch_tail_nb<float, 32>(const TailView<float> &, cudaStream_t);
-template cudaError_t prepare_nb<float, 32>();
 }  // namespace tail
 template void rows::launch_tail_rows<float, 24>(const TailView<float> &, cudaStream_t);
 template cudaError_t rows::prepare_rows<float, 24>();
-template void rows::launch_tail_rows<float, 32>(const TailView<float> &, cudaStream_t);
-template cudaError_t rows::prepare_rows<float, 32>();
 }  // namespace bm

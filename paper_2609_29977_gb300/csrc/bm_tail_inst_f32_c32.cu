@@ -1,0 +1,12 @@
+// Explicit instantiations of the tail factorization kernels (float, nb = 32).
+#include "bm_tail_factor.cuh"
+#include "bm_tail_rows.cuh"
+
+namespace bm {
+namespace tail {
+template void launch_tail_nb<float, 32>(const TailView<float> &, cudaStream_t);
+template cudaError_t prepare_nb<float, 32>();
+}  // namespace tail
+template void rows::launch_tail_rows<float, 32>(const TailView<float> &, cudaStream_t);
+template cudaError_t rows::prepare_rows<float, 32>();
+}  // namespace bm

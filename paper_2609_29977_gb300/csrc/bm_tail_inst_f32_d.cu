@@ -7,4 +7,6 @@ namespace tail {
 template void launch_tail_nb<float, 48>(const TailView<float> &, cudaStream_t);
 template cudaError_t prepare_nb<float, 48>();
 }  // namespace tail
+template void rows::launch_tail_rows_w<float, 48>(const TailView<float> &, cudaStream_t);
+template cudaError_t rows::prepare_rows_w<float, 48>();
 }  // namespace bm

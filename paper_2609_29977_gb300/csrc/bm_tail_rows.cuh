@@ -396,3 +396,373 @@ void launch_tail_rows(const TailView<T> &v, cudaStream_t st) {
 
 }  // namespace rows
 }  // namespace bm
+
+// ---------------------------------------------------------------------------
+// Wide variant for 32 < NB <= 64: a team of 64 lanes (two warps, named
+// barrier per team), lane i holding row i. Columns of the Cholesky factor
+// are exchanged through shared memory (two barriers per column); the
+// triangular solves read the finished factor from shared memory.
+// ---------------------------------------------------------------------------
+namespace bm {
+namespace rows {
+
+template <int NB>
+struct WCfg {
+  static constexpr int TS = 64;
+  static constexpr int LD = NB + 1;
+  static constexpr int SM = NB * LD;
+  // per-team shared memory (elements of T): staged block, factor, two column
+  // buffers, two pivot slots
+  static constexpr int ELEMS = 2 * SM + 2 * NB + 2;
+};
+
+__device__ __forceinline__ void team_bar(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
+
+template <typename T, int NB>
+__device__ __forceinline__ void stage_w(T *__restrict__ s, const T *__restrict__ g, int lane) {
+#pragma unroll
+  for (int e = lane; e < NB * NB; e += 64) {
+    const int r = e / NB, c = e - r * NB;
+    s[r * WCfg<NB>::LD + c] = g[e];
+  }
+}
+
+// Right-looking Cholesky on lane-owned rows with shared-memory exchange.
+template <typename T, int NB>
+__device__ __forceinline__ int chol_rows_w(T (&d)[NB], T &rinv, int i, T *sCol, T *sPiv, int bar) {
+  int fail = 0;
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    T *col = sCol + (j & 1) * NB;
+    if (i == j) sPiv[j & 1] = d[j];
+    team_bar(bar);
+    T piv = sPiv[j & 1];
+    if (!pivot_ok(piv)) {
+      if (!fail) fail = j + 1;
+      piv = T(1);
+    }
+    const T r = rsqrt_t<T>(piv);
+    if (i == j) {
+      d[j] = piv * r;
+      rinv = r;
+    } else {
+      d[j] *= r;
+    }
+    if (i < NB) col[i] = d[j];
+    team_bar(bar);
+#pragma unroll
+    for (int k = j + 1; k < NB; ++k) d[k] = fma_t<T>(-d[j], col[k], d[k]);
+  }
+  return fail;
+}
+
+// x := x L^{-T} for a lane-owned row, L staged in sL (row stride LD), sInv.
+template <typename T, int NB>
+__device__ __forceinline__ void trsm_row_w(T (&x)[NB], const T *sL, const T *sInv) {
+  constexpr int LD = WCfg<NB>::LD;
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    x[j] *= sInv[j];
+#pragma unroll
+    for (int k = j + 1; k < NB; ++k) x[k] = fma_t<T>(-x[j], sL[k * LD + j], x[k]);
+  }
+}
+
+template <typename T, int NB>
+__device__ __forceinline__ void syrk_row_w(T (&d)[NB], const T *__restrict__ sX, int ir) {
+  constexpr int LD = WCfg<NB>::LD;
+  T xi[NB];
+#pragma unroll
+  for (int k = 0; k < NB; ++k) xi[k] = sX[ir * LD + k];
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < NB; ++k) acc = fma_t<T>(xi[k], sX[j * LD + k], acc);
+    d[j] -= acc;
+  }
+}
+
+// One task of level lvl, wide team (sbuf: WCfg<NB>::ELEMS elements of T).
+template <typename T, int NB>
+__device__ __forceinline__ void factor_task_rows_w(const TailView<T> &v, T *sbuf, int lane, int bar, int s, int q,
+                                                   int lvl, bool elim) {
+  constexpr int NB2 = NB * NB, LD = WCfg<NB>::LD, SM = WCfg<NB>::SM;
+  T *sX = sbuf, *sL = sbuf + SM, *sCol = sL + SM, *sPiv = sCol + 2 * NB;
+  const int N = v.N;
+  const size_t sb = (size_t)s * N;
+  const int i = lane;
+  const bool act = i < NB;
+  const int ir = act ? i : 0;
+  T d[NB];
+  if (lvl <= 1) {
+    const double *Dq = v.D + (sb + (N - q)) * NB2;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) d[j] = to_t<T>(j <= ir ? Dq[ir * NB + j] : Dq[j * NB + ir]);
+  } else {
+    const T *Dq = v.Dt + (sb + (N - q)) * NB2 + ir * NB;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) d[j] = Dq[j];
+  }
+  if (lvl >= 1) {
+    const int h = 1 << (lvl - 1);
+    int pl = 0, pr = 0;
+    if (q < N) {
+      pl = q - h;
+      if (q + h <= N - 1) pr = q + h;
+    } else {
+      const int m = ((N - 1) >> (lvl - 1)) << (lvl - 1);
+      if (ctz32(m) == lvl - 1) pl = m;
+    }
+    if (pl) {
+      stage_w<T, NB>(sX, v.Lr + (sb + (N - pl)) * NB2, lane);
+      team_bar(bar);
+      syrk_row_w<T, NB>(d, sX, ir);
+      team_bar(bar);
+    }
+    if (pr) {
+      stage_w<T, NB>(sX, v.Ll + (sb + (N - pr)) * NB2, lane);
+      team_bar(bar);
+      syrk_row_w<T, NB>(d, sX, ir);
+      team_bar(bar);
+    }
+  }
+  if (!elim) {
+    if (act) {
+      T *o = v.Dt + (sb + (N - q)) * NB2 + i * NB;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) o[j] = d[j];
+    }
+    return;
+  }
+  const int hh = 1 << lvl;
+  const bool hasA = q > hh;
+  const int a = q - hh;
+  T rinv = T(1);
+  const int fail = chol_rows_w<T, NB>(d, rinv, i, sCol, sPiv, bar);
+  if (i == 0 && fail) report_not_spd(v.status, s, N + 1 - q);
+  if (act) {
+    T *Ld = v.Ld + (sb + (N - q)) * NB2 + i * NB;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const T l = j <= i ? d[j] : T(0);
+      Ld[j] = l;
+      sL[i * LD + j] = l;
+    }
+    sCol[i] = rinv;   // inverse diagonal (column buffers are free now)
+    v.invd[(sb + (N - q)) * NB + i] = rinv;
+  }
+  team_bar(bar);
+  // left coupling: L_{a,q} = M_{a,q} L^{-T}, staged for the fill
+  if (hasA) {
+    T av[NB];
+    if (lvl == 0) {
+      const double *Ea = v.E + ((size_t)s * (N - 1) + (N - q)) * NB2 + ir * NB;
+#pragma unroll
+      for (int k = 0; k < NB; ++k) av[k] = to_t<T>(Ea[k]);
+    } else {
+      const T *Wa = v.W + (sb + (N - a)) * NB2;
+#pragma unroll
+      for (int k = 0; k < NB; ++k) av[k] = Wa[k * NB + ir];
+    }
+    trsm_row_w<T, NB>(av, sL, sCol);
+    if (act) {
+      T *La = v.Ll + (sb + (N - q)) * NB2 + i * NB;
+#pragma unroll
+      for (int k = 0; k < NB; ++k) {
+        La[k] = av[k];
+        sX[i * LD + k] = av[k];
+      }
+    }
+  } else if (act) {
+    T *La = v.Ll + (sb + (N - q)) * NB2 + i * NB;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) La[k] = T(0);
+  }
+  // right coupling: L_{b,q} = M_{b,q} L^{-T}
+  T b[NB];
+  if (lvl == 0 || q == N - 1) {
+    const double *Eb = v.E + ((size_t)s * (N - 1) + (N - q - 1)) * NB2;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) b[k] = to_t<T>(Eb[k * NB + ir]);
+  } else {
+    const T *Wb = v.W + (sb + (N - q)) * NB2 + ir * NB;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) b[k] = Wb[k];
+  }
+  trsm_row_w<T, NB>(b, sL, sCol);
+  if (act) {
+    T *Lb = v.Lr + (sb + (N - q)) * NB2 + i * NB;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) Lb[k] = b[k];
+  }
+  if (hasA) {
+    team_bar(bar);
+    if (act) {
+      T *Wo = v.W + (sb + (N - a)) * NB2 + i * NB;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        T acc = T(0);
+#pragma unroll
+        for (int k = 0; k < NB; ++k) acc = fma_t<T>(b[k], sX[j * LD + k], acc);
+        Wo[j] = -acc;
+      }
+    }
+  }
+  team_bar(bar);
+}
+
+// x_1 of tail s with a wide team. sbuf: x1_rows_w_bytes bytes.
+template <typename T, int NB>
+__host__ __device__ constexpr size_t x1_rows_w_bytes(int nr) {
+  return (size_t)nr * NB * sizeof(double) + (size_t)WCfg<NB>::ELEMS * sizeof(T);
+}
+
+template <typename T, int NB>
+__device__ __forceinline__ void x1_task_rows_w(const TailView<T> &v, void *sbuf, int lane, int bar, int s) {
+  constexpr int NB2 = NB * NB, LD = WCfg<NB>::LD, SM = WCfg<NB>::SM;
+  const int N = v.N, nr = v.nr, Lc = v.Lc;
+  const size_t sb = (size_t)s * N;
+  double *sC = (double *)sbuf;
+  T *sX = (T *)(sC + nr * NB), *sL = sX + SM, *sCol = sL + SM, *sPiv = sCol + 2 * NB;
+  const int i = lane;
+  const bool act = i < NB;
+  const int ir = act ? i : 0;
+  T d[NB];
+  if (Lc <= 1) {
+    const double *Dq = v.D + sb * NB2;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) d[j] = to_t<T>(j <= ir ? Dq[ir * NB + j] : Dq[j * NB + ir]);
+  } else {
+    const T *Dq = v.Dt + sb * NB2 + ir * NB;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) d[j] = Dq[j];
+  }
+  if (Lc >= 1) {
+    const int m = 1 << (Lc - 1);
+    stage_w<T, NB>(sX, v.Lr + (sb + (N - m)) * NB2, lane);
+    team_bar(bar);
+    syrk_row_w<T, NB>(d, sX, ir);
+    team_bar(bar);
+  }
+  T rinv = T(1);
+  const int fail = chol_rows_w<T, NB>(d, rinv, i, sCol, sPiv, bar);
+  if (i == 0 && fail) report_not_spd(v.status, s, 1);
+  if (act) {
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const T l = j <= i ? d[j] : T(0);
+      v.Ld[sb * NB2 + i * NB + j] = l;
+      sL[i * LD + j] = l;
+      v.Lr[sb * NB2 + i * NB + j] = T(0);
+      v.Ll[sb * NB2 + i * NB + j] = T(0);
+    }
+    v.invd[sb * NB + i] = rinv;
+  }
+  team_bar(bar);
+  if (act) sCol[i] = rinv;
+  for (int e = lane; e < nr * NB; e += 64) sC[e] = v.C[(size_t)s * nr * NB + e];
+  team_bar(bar);
+  for (int c = lane; c < nr; c += 64) {
+    double f[NB];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) f[k] = sC[c * NB + k];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      f[j] *= to_d<T>(sCol[j]);
+#pragma unroll
+      for (int k = j + 1; k < NB; ++k) f[k] = fma(-f[j], to_d<T>(sL[k * LD + j]), f[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+      sC[c * NB + k] = f[k];
+      v.F[(size_t)s * nr * NB + c * NB + k] = f[k];
+    }
+  }
+  team_bar(bar);
+  double *Us = v.U + (size_t)s * nr * nr;
+  for (int e = lane; e < nr * nr; e += 64) {
+    const int a = e / nr, b = e - a * nr;
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) acc = fma(sC[a * NB + k], sC[b * NB + k], acc);
+    Us[e] = acc;
+  }
+}
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(128) k_level_rows_w(TailView<T> v, int lvl) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int team = threadIdx.x / 64, lane = threadIdx.x % 64;
+  T *sb = (T *)smem_raw + team * WCfg<NB>::ELEMS;
+  const int N = v.N, S = v.S;
+  const int E = level_elims(N, lvl);
+  const int G = lvl == 0 ? 0 : ((N - 1) >> (lvl + 1)) + 1;
+  const long g = (long)blockIdx.x * (blockDim.x / 64) + team;
+  pdl_wait();
+  if (g < (long)S * (E + G)) {
+    int s, q;
+    bool elim;
+    if (g < (long)S * E) {
+      s = (int)(g / E);
+      q = (2 * (int)(g - (long)s * E) + 1) << lvl;
+      elim = true;
+    } else {
+      const long g2 = g - (long)S * E;
+      s = (int)(g2 / G);
+      const int j = (int)(g2 - (long)s * G);
+      q = j < G - 1 ? (j + 1) << (lvl + 1) : N;
+      elim = false;
+    }
+    factor_task_rows_w<T, NB>(v, sb, lane, 1 + team, s, q, lvl, elim);
+  }
+  pdl_trigger();
+}
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) k_top_rows_w(TailView<T> v, int lvl0) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int team = threadIdx.x / 64, lane = threadIdx.x % 64, teams = blockDim.x / 64;
+  T *sb = (T *)smem_raw + team * WCfg<NB>::ELEMS;
+  const int N = v.N, s = blockIdx.x;
+  pdl_wait();
+  for (int lvl = lvl0; lvl < v.Lc; ++lvl) {
+    const int E = level_elims(N, lvl);
+    const int G = lvl == 0 ? 0 : ((N - 1) >> (lvl + 1)) + 1;
+    for (int t = team; t < E + G; t += teams) {
+      const bool elim = t < E;
+      const int q = elim ? (2 * t + 1) << lvl : (t - E < G - 1 ? (t - E + 1) << (lvl + 1) : N);
+      factor_task_rows_w<T, NB>(v, sb, lane, 1 + team, s, q, lvl, elim);
+    }
+    __syncthreads();
+  }
+  if (team == 0) x1_task_rows_w<T, NB>(v, smem_raw, lane, 1, s);
+  pdl_trigger();
+}
+
+template <typename T, int NB>
+cudaError_t prepare_rows_w() {
+  cudaError_t e = cudaFuncSetAttribute(k_level_rows_w<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 120 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_top_rows_w<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+template <typename T, int NB>
+void launch_tail_rows_w(const TailView<T> &v, cudaStream_t st) {
+  const int Tl = top_level(v.N);
+  const size_t per = (size_t)WCfg<NB>::ELEMS * sizeof(T);
+  for (int l = 0; l < Tl; ++l) {
+    const int E = level_elims(v.N, l);
+    const int G = l == 0 ? 0 : ((v.N - 1) >> (l + 1)) + 1;
+    const long tasks = (long)v.S * (E + G);
+    const long blocks = (tasks + 1) / 2;
+    launch_pdl(k_level_rows_w<T, NB>, (unsigned)blocks, 128, 2 * per, st, v, l);
+  }
+  size_t smem = 4 * per;
+  const size_t x1b = x1_rows_w_bytes<T, NB>(v.nr);
+  if (x1b > smem) smem = x1b;
+  launch_pdl(k_top_rows_w<T, NB>, (unsigned)v.S, 256, smem, st, v, Tl);
+}
+
+}  // namespace rows
+}  // namespace bm

@@ -27,7 +27,7 @@ struct Team {
     lane = threadIdx.x % TEAM;
     id = threadIdx.x / TEAM;
     if (TEAM < 32)
-      mask = ((1u << TEAM) - 1u) << ((threadIdx.x & 31) / TEAM * TEAM);
+      mask = ((1u << (TEAM & 31)) - 1u) << ((threadIdx.x & 31) / TEAM * TEAM);
     else
       mask = 0xffffffffu;
   }
