@@ -317,6 +317,153 @@ def run_batched(args):
     return 0
 
 
+def _percentile(vals, q):
+    v = sorted(vals)
+    if not v:
+        return None
+    k = (len(v) - 1) * q
+    lo = int(k)
+    hi = min(lo + 1, len(v) - 1)
+    return v[lo] + (v[hi] - v[lo]) * (k - lo)
+
+
+def run_serving(args):
+    """Serving: a Poisson stream of requests (mean --rate per second), each a
+    branch-MPC system drawn as in the batched workload (S~U{8..256},
+    N~U{16..256}, nb in {6,12,24,48}, nr = ceil(nb/3)) or, with probability
+    5%, the large system (S=2048, N=256, nb=48, nr=16); every request is
+    factored once and solved for 4 right-hand sides against its resident
+    factor. The requests go through the library's serving runtime (admission
+    by an HBM budget, one stream per slot), first with the FP32-tail +
+    refinement path, then with the plain FP64 path, on the same arrival
+    trace; then both again at half the throughput the first run sustained.
+    The inputs of a request are drawn from a pool of distinct systems and are
+    resident in HBM before the stream starts; latency = completion of the
+    last solve - arrival."""
+    import random
+
+    import torch
+
+    import bmgen
+    import paper_2609_29977_gb300 as bm
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    rng = random.Random(args.seed)
+    nrhs = 4
+    t0 = time.perf_counter()
+    small_shapes = bmgen.draw_batched_shapes(args.pool, seed=5000)
+    base = bmgen.Workload("serve", 1, 1, 1, 1, workload_id=7, barrier=(-4.0, 4.0), shared_A=True)
+    pool = []
+    for j, (S, N, nb, nr) in enumerate(small_shapes):
+        pool.append(bmgen.generate(base.with_shape(S=S, N=N, nb=nb, nr=nr), instance=j, device=dev, with_rhs=False))
+    large_w = bmgen.WORKLOADS["large-s2048-n256-nb48"]
+    if args.large_frac > 0:
+        pool.append(bmgen.generate(large_w, device=dev, with_rhs=False))
+    for j, d in enumerate(pool):
+        n = bmgen.n_unknowns(d["S"], d["N"], d["nb"], d["nr"])
+        g = torch.Generator(device=dev).manual_seed(9000 + j)
+        d["rs"] = torch.randn((nrhs, n), generator=g, device=dev, dtype=torch.float64)
+    gen_s = time.perf_counter() - t0
+    n_small = len(small_shapes)
+    kinds = []
+    for _ in range(args.requests):
+        if args.large_frac > 0 and rng.random() < args.large_frac:
+            kinds.append(n_small)
+        else:
+            kinds.append(rng.randrange(n_small))
+    gaps = [rng.expovariate(1.0) for _ in range(args.requests)]   # unit-rate gaps, scaled per run
+    flops = []
+    for k in kinds:
+        d = pool[k]
+        f = bmgen.method_flops(d["S"], d["N"], d["nb"], d["nr"])
+        flops.append(f["factor"] + nrhs * f["solve"])
+    xs = [torch.empty_like(pool[k]["rs"]) for k in kinds]
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    budget = int(args.serve_budget_gb * (1 << 30))
+
+    def one_run(precision, rate):
+        server = bm.BranchKKTServer(budget, slots=args.slots, precision=precision, max_refine=args.max_refine,
+                                    tol=args.tol)
+
+        def submit(rid, k, x):
+            d = pool[k]
+            server.submit(rid, d["S"], d["N"], d["nb"], d["nr"], d["D"], d["E"], d["C"], d["R"], d["rs"], x)
+
+        # warm-up: every distinct system once (kernel attributes, allocator)
+        for j in range(len(pool)):
+            submit(10 ** 9 + j, j, torch.empty_like(pool[j]["rs"]))
+        server.drain()
+        arrivals, t = [], 0.0
+        for gp in gaps:
+            t += gp / rate
+            arrivals.append(t)
+        sampler = ClockSampler("0")
+        sampler.start()
+        time.sleep(0.3)
+        comps, delay = {}, {}
+        i = 0
+        start = time.perf_counter()
+        while len(comps) < args.requests:
+            now = time.perf_counter() - start
+            while i < args.requests and arrivals[i] <= now:
+                submit(i, kinds[i], xs[i])
+                delay[i] = (time.perf_counter() - start) - arrivals[i]
+                i += 1
+            for c in server.poll(wait=(i >= args.requests)):
+                comps[c["id"]] = c
+        wall = time.perf_counter() - start
+        clocks = sampler.stop()
+        stats = server.stats()
+        server.close()
+        lat, bad, etas = [], 0, []
+        first_submit = min(c["t_submit_us"] - delay[c["id"]] * 1e6 for c in comps.values())
+        last_done = max(c["t_done_us"] for c in comps.values())
+        for rid, c in comps.items():
+            # arrival on the server's clock = submission - how late the submission was
+            arrival_us = c["t_submit_us"] - delay[rid] * 1e6
+            lat.append((c["t_done_us"] - arrival_us) * 1e-3)
+            bad += c["status"] != 0
+            etas += [e for e in c["backward_error"] if e >= 0]
+        span_s = (last_done - first_submit) * 1e-6
+        # the solutions of a sample of requests against plain PyTorch FP64 residuals
+        sample_eta = 0.0
+        for rid in range(min(8, args.requests)):
+            d = pool[kinds[rid]]
+            gd = {"D": d["D"], "E": d["E"], "C": d["C"], "R": d["R"], "r": d["rs"][0]}
+            sample_eta = max(sample_eta, gpu_backward_error(gd, xs[rid][0])[0])
+        return {"offered_rate": rate, "throughput_req_s": args.requests / span_s,
+                "gflops": sum(flops) / span_s / 1e9, "p50_ms": _percentile(lat, 0.5), "p99_ms": _percentile(lat, 0.99),
+                "max_ms": max(lat), "makespan_s": span_s, "wall_s": wall, "failed": bad,
+                "device_backward_error_max": max(etas) if etas else None, "sample_backward_error_max": sample_eta,
+                "peak_arena_gb": stats["peak_bytes_in_use"] / 2 ** 30, "clocks": clocks}
+
+    runs = {}
+    runs["fp32ir"] = one_run(bm.BM_PREC_FP32_IR, args.rate)
+    runs["fp64"] = one_run(bm.BM_PREC_FP64, args.rate)
+    half = 0.5 * runs["fp32ir"]["throughput_req_s"]
+    runs["fp32ir_half_load"] = one_run(bm.BM_PREC_FP32_IR, half)
+    runs["fp64_half_load"] = one_run(bm.BM_PREC_FP64, half)
+    main = runs["fp32ir"]
+    line = {
+        "metric": "serving: requests/s (factor + 4 RHS per request) with p50/p99 latency; FP32+IR vs FP64",
+        "value": main["throughput_req_s"], "unit": "req/s", "n_gpus": 1, "steps": args.requests, "warmup": len(pool),
+        "ms_per_step": 1e3 * main["makespan_s"] / args.requests, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (seeded MPC-shaped generator)",
+        "config": {"workload": "serving-poisson-%g-per-s" % args.rate, "requests": args.requests,
+                   "large_fraction": args.large_frac, "pool_small_systems": n_small, "rhs_per_request": nrhs,
+                   "slots": args.slots, "hbm_budget_gb": args.serve_budget_gb, "tol": args.tol,
+                   "l2": "inputs of the stream (pool of %d systems, %.1f GB) exceed L2" %
+                         (len(pool), sum(sum(d[k].numel() for k in ("D", "E")) * 8 for d in pool) / 1e9)},
+        "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"], "runs": runs,
+        "throughput_vs_fp64": main["throughput_req_s"] / runs["fp64"]["throughput_req_s"],
+        "generate_s": gen_s,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_gpu(args):
     import torch
 
@@ -450,6 +597,32 @@ def run_gpu(args):
                                 "kind": "oracle",
                                 "sample": "full workload factor+solve x%d (%.1f s)" % (reps, sec * reps)}
     solver.close()
+    if args.precision == "fp64" and not args.no_fp32ir_compare:
+        # the FP32-tail + FP64-refinement path on the same system, same timing
+        mixed = bm.BranchKKTSolver(w.S, w.N, w.nb, w.nr, precision=bm.BM_PREC_FP32_IR,
+                                   max_refine=args.max_refine, tol=args.tol)
+        xm = torch.empty_like(g["r"])
+        for _ in range(max(3, args.warmup)):
+            mixed.factor(g["D"], g["E"], g["C"], g["R"])
+            mixed.solve(g["r"], xm)
+        k = min(args.steps, 1000)
+        evm = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        torch.cuda.synchronize()
+        for a, b in evm:
+            flush.zero_()
+            a.record(stream)
+            mixed.factor(g["D"], g["E"], g["C"], g["R"])
+            mixed.solve(g["r"], xm)
+            b.record(stream)
+        torch.cuda.synchronize()
+        mms = statistics.mean(a.elapsed_time(b) for a, b in evm)
+        minfo = mixed.query()
+        meta, mrel = gpu_backward_error(g, xm)
+        line["fp32ir_same_workload"] = {
+            "us_per_kkt": mms * 1e3, "value": world * fl["total"] / (mms * 1e-3) / 1e9, "unit": "GFLOP/s",
+            "steps": k, "backward_error": meta, "rel_residual": mrel, "refinement_steps": minfo["iters"],
+            "device_status": minfo["name"], "speedup_vs_fp64": ms_per_step / mms}
+        mixed.close()
     if dist:
         dist.destroy_process_group()
     if rank == 0:
@@ -472,11 +645,21 @@ def main():
     ap.add_argument("--shape", default="", help="S,N,nb,nr override of the workload's shape (profiling)")
     ap.add_argument("--batch-count", type=int, default=256, help="systems in the batched workload")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-fp32ir-compare", action="store_true")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean Poisson arrivals per second")
+    ap.add_argument("--requests", type=int, default=200, help="serving: requests per run")
+    ap.add_argument("--pool", type=int, default=24, help="serving: distinct small systems")
+    ap.add_argument("--large-frac", type=float, default=0.05, help="serving: fraction of large requests")
+    ap.add_argument("--slots", type=int, default=8, help="serving: requests in flight at most")
+    ap.add_argument("--serve-budget-gb", type=float, default=160.0, help="serving: HBM arena")
+    ap.add_argument("--seed", type=int, default=2000)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload.startswith("batched"):
         return run_batched(args)
+    if args.workload.startswith("serving"):
+        return run_serving(args)
     return run_gpu(args)
 
 

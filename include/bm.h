@@ -272,6 +272,99 @@ void bm_batch_destroy(bm_batch b);
 /* Frees everything the handle owns (synchronizes its internal stream). */
 void bm_destroy(bm_handle h);
 
+/* ---------------------------------------------------------------------------
+ * Serving runtime: a request loop that admits independent branch-MPC solves
+ * by device memory, runs each admitted request (one factor of Alg. 1, then
+ * nrhs solves of Alg. 2 against the resident factor) on its own stream slot
+ * so that the work of requests admitted at different times overlaps on the
+ * GPU, and reports per-request latency. Not in the paper: the paper solves
+ * one system at a time. A request is computed exactly as bm_factor /
+ * bm_solve compute it alone (same kernels, same launch shapes, which depend
+ * only on the request's shape), so its result does not depend on what else
+ * is in flight.
+ *
+ * Admission is first-in first-out: the request at the head of the queue is
+ * admitted as soon as a slot is free and a contiguous range of the server's
+ * device arena (hbm_budget bytes, allocated once at creation) can hold
+ * bm_server_request_bytes of it; requests behind a blocked head wait.
+ * Memory and slot are released when the request's last copy has finished.
+ * A server is driven by one host thread (no internal threads); every call
+ * below advances it without blocking on the device unless it says so.
+ * ------------------------------------------------------------------------- */
+typedef struct bm_server_s *bm_server;
+
+#define BM_SERVE_MAX_RHS 8
+#define BM_SERVE_MAX_SLOTS 64
+
+/* D, E, C, R, r are HOST pointers (page-locked memory recommended, else the
+ * copies serialize the host), x a host output buffer; the server stages
+ * them through its arena and copies x back before the request completes. */
+#define BM_REQ_HOST_IO 1
+
+typedef struct {
+  size_t hbm_budget; /* bytes of device memory for admitted requests (> 0) */
+  int slots;         /* requests in flight at most, 1..BM_SERVE_MAX_SLOTS; one stream each */
+  int precision;     /* bm_precision, for every request of the server */
+  int max_refine;    /* as bm_desc.max_refine (mixed precision) */
+  double tol;        /* as bm_desc.tol */
+} bm_server_desc;
+
+typedef struct {
+  unsigned long long id; /* caller's tag, returned in the completion */
+  int S, N, nb, nr;      /* system shape, limits as in bm_desc */
+  int nrhs;              /* right-hand sides solved against the factor, 1..BM_SERVE_MAX_RHS */
+  int flags;             /* 0 or BM_REQ_HOST_IO */
+  const double *D, *E, *C, *R; /* layouts as for bm_factor; E may be NULL when N = 1 */
+  const double *r;       /* nrhs right-hand sides of n = S*N*nb + nr values, back to back */
+  double *x;             /* nrhs solutions, same layout (must not overlap r) */
+} bm_request;
+
+typedef struct {
+  unsigned long long id;
+  int status;            /* first non-OK status over factor and solves (bm_status) */
+  int fail_scenario;     /* as bm_info, for BM_ERR_NOT_SPD */
+  int fail_stage;
+  int iters[BM_SERVE_MAX_RHS];           /* refinement steps per right-hand side */
+  double backward_error[BM_SERVE_MAX_RHS]; /* device estimate per rhs (mixed; -1 for FP64) */
+  /* microseconds since bm_server_create: submission (host clock), start of
+   * the request's first copy or kernel, end of its factor, end of its last
+   * solve/copy (device event clock) */
+  double t_submit_us, t_start_us, t_factor_us, t_done_us;
+} bm_completion;
+
+typedef struct {
+  unsigned long long submitted, admitted, completed;
+  int queued, in_flight;
+  size_t bytes_in_use, peak_bytes_in_use, budget;
+} bm_server_stats;
+
+/* Arena bytes a request holds while in flight (its factor workspace as
+ * bm_workspace_bytes, plus the staging of its inputs and outputs under
+ * BM_REQ_HOST_IO), or 0 if the request is malformed for this server. */
+size_t bm_server_request_bytes(const bm_server_desc *desc, const bm_request *req);
+
+/* Allocates the arena and the slots' streams and events.
+ * Errors: BM_ERR_INVALID_ARG, BM_ERR_OOM (arena), BM_ERR_CUDA. */
+bm_status bm_server_create(const bm_server_desc *desc, bm_server *out);
+
+/* Queues a request (the caller keeps its buffers valid until its completion
+ * is returned) and admits what fits. BM_ERR_INVALID_ARG: malformed request,
+ * or one larger than the whole budget (it could never be admitted). */
+bm_status bm_server_submit(bm_server s, const bm_request *req);
+
+/* Retires finished requests, admits queued ones and writes up to max_out
+ * completions (oldest first) to out; *n_out = how many. Does not block
+ * unless wait != 0, in which case it waits until at least one completion
+ * is available or nothing is queued or in flight. */
+bm_status bm_server_poll(bm_server s, int wait, bm_completion *out, int max_out, int *n_out);
+
+/* Counters of the server; may be called at any time. */
+bm_status bm_server_get_stats(bm_server s, bm_server_stats *out);
+
+/* Waits for the requests in flight, then frees everything; queued requests
+ * that were never admitted are dropped. */
+void bm_server_destroy(bm_server s);
+
 #ifdef __cplusplus
 }
 #endif

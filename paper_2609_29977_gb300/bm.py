@@ -26,9 +26,13 @@ EXPORTED_SYMBOLS = ("bm_version", "bm_status_string", "bm_workspace_bytes", "bm_
                     "bm_solve", "bm_query", "bm_export_factor", "bm_factor_solve_host", "bm_destroy",
                     "bm_factor_solve_noalloc", "bm_round_to_fp32", "bm_batch_workspace_bytes",
                     "bm_batch_analyze", "bm_batch_factor", "bm_batch_solve", "bm_batch_query",
-                    "bm_batch_schedule", "bm_batch_destroy")
+                    "bm_batch_schedule", "bm_batch_destroy", "bm_server_request_bytes", "bm_server_create",
+                    "bm_server_submit", "bm_server_poll", "bm_server_get_stats", "bm_server_destroy")
 BATCH_NB = (4, 6, 12, 24, 48)
 BM_NOALLOC_SCRATCH_BYTES = 32 << 20
+BM_SERVE_MAX_RHS = 8
+BM_SERVE_MAX_SLOTS = 64
+BM_REQ_HOST_IO = 1
 
 
 class bm_desc(ctypes.Structure):
@@ -40,6 +44,32 @@ class bm_desc(ctypes.Structure):
 class bm_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("fail_scenario", ctypes.c_int), ("fail_stage", ctypes.c_int),
                 ("iters", ctypes.c_int), ("backward_error", ctypes.c_double)]
+
+
+class bm_server_desc(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("slots", ctypes.c_int), ("precision", ctypes.c_int),
+                ("max_refine", ctypes.c_int), ("tol", ctypes.c_double)]
+
+
+class bm_request(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_ulonglong), ("S", ctypes.c_int), ("N", ctypes.c_int), ("nb", ctypes.c_int),
+                ("nr", ctypes.c_int), ("nrhs", ctypes.c_int), ("flags", ctypes.c_int),
+                ("D", ctypes.c_void_p), ("E", ctypes.c_void_p), ("C", ctypes.c_void_p), ("R", ctypes.c_void_p),
+                ("r", ctypes.c_void_p), ("x", ctypes.c_void_p)]
+
+
+class bm_completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_ulonglong), ("status", ctypes.c_int), ("fail_scenario", ctypes.c_int),
+                ("fail_stage", ctypes.c_int), ("iters", ctypes.c_int * BM_SERVE_MAX_RHS),
+                ("backward_error", ctypes.c_double * BM_SERVE_MAX_RHS), ("t_submit_us", ctypes.c_double),
+                ("t_start_us", ctypes.c_double), ("t_factor_us", ctypes.c_double), ("t_done_us", ctypes.c_double)]
+
+
+class bm_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_ulonglong), ("admitted", ctypes.c_ulonglong),
+                ("completed", ctypes.c_ulonglong), ("queued", ctypes.c_int), ("in_flight", ctypes.c_int),
+                ("bytes_in_use", ctypes.c_size_t), ("peak_bytes_in_use", ctypes.c_size_t),
+                ("budget", ctypes.c_size_t)]
 
 
 class BMError(RuntimeError):
@@ -103,6 +133,19 @@ def _load():
     lib.bm_round_to_fp32.argtypes = [dp, dp, ctypes.c_size_t, vp]
     lib.bm_factor_solve_noalloc.restype = ctypes.c_int
     lib.bm_factor_solve_noalloc.argtypes = [ctypes.c_int] * 4 + [dp] * 6 + [vp]
+    lib.bm_server_request_bytes.restype = sz
+    lib.bm_server_request_bytes.argtypes = [ctypes.POINTER(bm_server_desc), ctypes.POINTER(bm_request)]
+    lib.bm_server_create.restype = ctypes.c_int
+    lib.bm_server_create.argtypes = [ctypes.POINTER(bm_server_desc), ctypes.POINTER(vp)]
+    lib.bm_server_submit.restype = ctypes.c_int
+    lib.bm_server_submit.argtypes = [vp, ctypes.POINTER(bm_request)]
+    lib.bm_server_poll.restype = ctypes.c_int
+    lib.bm_server_poll.argtypes = [vp, ctypes.c_int, ctypes.POINTER(bm_completion), ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_int)]
+    lib.bm_server_get_stats.restype = ctypes.c_int
+    lib.bm_server_get_stats.argtypes = [vp, ctypes.POINTER(bm_server_stats)]
+    lib.bm_server_destroy.restype = None
+    lib.bm_server_destroy.argtypes = [vp]
     _lib = lib
     return lib
 
@@ -381,6 +424,113 @@ class BranchKKTBatch:
         if self.h:
             bm_batch_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --------------------------------------------------------------------------
+# Serving runtime (include/bm.h, "Serving runtime")
+
+def make_server_desc(hbm_budget, slots=8, precision=BM_PREC_FP32_IR, max_refine=10, tol=1e-10) -> bm_server_desc:
+    return bm_server_desc(int(hbm_budget), int(slots), int(precision), int(max_refine), float(tol))
+
+
+def _request(rid, S, N, nb, nr, D, E, C, R, r, x, host_io):
+    dev = not host_io
+    nrhs = r.shape[0] if r.dim() == 2 else 1
+    return bm_request(int(rid), int(S), int(N), int(nb), int(nr), int(nrhs), BM_REQ_HOST_IO if host_io else 0,
+                      _ptr(D, "D", dev), _ptr(E, "E", dev) if N > 1 else None, _ptr(C, "C", dev),
+                      _ptr(R, "R", dev), _ptr(r, "r", dev), _ptr(x, "x", dev))
+
+
+def bm_server_request_bytes(desc: bm_server_desc, req: bm_request) -> int:
+    return int(_load().bm_server_request_bytes(ctypes.byref(desc), ctypes.byref(req)))
+
+
+def bm_server_create(desc: bm_server_desc) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(_load().bm_server_create(ctypes.byref(desc), ctypes.byref(h)), "bm_server_create")
+    return h
+
+
+def bm_server_submit(s, req: bm_request) -> None:
+    _check(_load().bm_server_submit(s, ctypes.byref(req)), "bm_server_submit")
+
+
+def _completion_dict(c: bm_completion, nrhs: int) -> dict:
+    return {"id": int(c.id), "status": int(c.status), "fail_scenario": int(c.fail_scenario),
+            "fail_stage": int(c.fail_stage), "iters": [int(c.iters[j]) for j in range(nrhs)],
+            "backward_error": [float(c.backward_error[j]) for j in range(nrhs)],
+            "t_submit_us": float(c.t_submit_us), "t_start_us": float(c.t_start_us),
+            "t_factor_us": float(c.t_factor_us), "t_done_us": float(c.t_done_us)}
+
+
+def bm_server_poll(s, wait=False, max_out=256) -> list:
+    buf = (bm_completion * max_out)()
+    n = ctypes.c_int(0)
+    _check(_load().bm_server_poll(s, 1 if wait else 0, buf, max_out, ctypes.byref(n)), "bm_server_poll")
+    return [buf[i] for i in range(n.value)]
+
+
+def bm_server_get_stats(s) -> dict:
+    st = bm_server_stats()
+    _check(_load().bm_server_get_stats(s, ctypes.byref(st)), "bm_server_get_stats")
+    return {k: int(getattr(st, k)) for k, _ in bm_server_stats._fields_}
+
+
+def bm_server_destroy(s) -> None:
+    _load().bm_server_destroy(s)
+
+
+class BranchKKTServer:
+    """A request loop over one GPU: admits requests by device memory (first in,
+    first out), keeps each request's factor resident while its right-hand
+    sides are solved, and overlaps admitted requests on separate streams.
+    Tensors of a request are held here until its completion is returned.
+    """
+
+    def __init__(self, hbm_budget, slots=8, precision=BM_PREC_FP32_IR, max_refine=10, tol=1e-10):
+        self.desc = make_server_desc(hbm_budget, slots, precision, max_refine, tol)
+        self.h = bm_server_create(self.desc)
+        self._held = {}
+
+    def request_bytes(self, S, N, nb, nr, D, E, C, R, r, x, host_io=False) -> int:
+        return bm_server_request_bytes(self.desc, _request(0, S, N, nb, nr, D, E, C, R, r, x, host_io))
+
+    def submit(self, rid, S, N, nb, nr, D, E, C, R, r, x, host_io=False) -> None:
+        """r, x: [nrhs, S*N*nb + nr] (or one vector); device tensors, or host
+        tensors (page-locked for speed) with host_io=True."""
+        if rid in self._held:
+            raise ValueError("request id %r is already in flight" % (rid,))
+        req = _request(rid, S, N, nb, nr, D, E, C, R, r, x, host_io)
+        bm_server_submit(self.h, req)
+        self._held[rid] = (D, E, C, R, r, x, req.nrhs)
+
+    def poll(self, wait=False) -> list:
+        out = []
+        for c in bm_server_poll(self.h, wait):
+            nrhs = self._held.pop(int(c.id))[6]
+            out.append(_completion_dict(c, nrhs))
+        return out
+
+    def drain(self) -> list:
+        out = []
+        while self._held:
+            out.extend(self.poll(wait=True))
+        return out
+
+    def stats(self) -> dict:
+        return bm_server_get_stats(self.h)
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            bm_server_destroy(self.h)
+        self.h = None
+        self._held = {}
 
     def __del__(self):
         try:

@@ -22,7 +22,7 @@ struct MixedState;
 size_t mixed_bytes(int S, int N, int nb, int nr);
 cudaError_t mixed_prepare(int nb, int nr);
 MixedState *mixed_create(int S, int N, int nb, int nr, void *base, size_t bytes, Status *status,
-                         unsigned *tickets);
+                         unsigned *tickets, cudaStream_t init_stream, bool sync_init);
 void mixed_destroy(MixedState *m);
 void mixed_launch_factor(MixedState *m, const double *D, const double *E, const double *C,
                          const double *R, cudaStream_t st);
@@ -45,6 +45,7 @@ struct bm_handle_s {
   int device = 0;
   void *pool = nullptr;
   size_t pool_bytes = 0;
+  bool owns_pool = true;
   F64View v{};           // FP64 buffers (unused pointers null in mixed mode)
   double *r0t = nullptr; // [nr] root right-hand side scratch
   Status *status = nullptr;
@@ -107,34 +108,47 @@ extern "C" size_t bm_workspace_bytes(const bm_desc *d) {
   return t;
 }
 
-extern "C" bm_status bm_analyze(const bm_desc *desc, void *stream, bm_handle *out) {
-  (void)stream;
+// Builds a handle over `mem` (bytes >= bm_workspace_bytes) or, when mem is
+// null, over memory it allocates and owns. light = true skips the graph
+// capture stream and every synchronizing call (used by the serving loop,
+// which launches without graphs on its own streams); initialization is then
+// ordered on init_stream.
+bm_status analyze_impl(const bm_desc *desc, void *mem, size_t bytes, cudaStream_t init_stream, bool light,
+                       bm_handle *out) {
   if (!out) return BM_ERR_INVALID_ARG;
   *out = nullptr;
   if (!valid_desc(desc)) return BM_ERR_INVALID_ARG;
+  const size_t need = bm_workspace_bytes(desc);
+  if (mem && bytes < need) return BM_ERR_INVALID_ARG;
   bm_handle h = new (std::nothrow) bm_handle_s();
   if (!h) return BM_ERR_OOM;
   h->desc = *desc;
   if (h->desc.max_refine <= 0) h->desc.max_refine = 10;
   if (!(h->desc.tol > 0.0)) h->desc.tol = 1e-10;
+  if (light) h->desc.flags |= BM_FLAG_NO_GRAPH;
   const int S = desc->S, N = desc->N, nb = desc->nb, nr = desc->nr;
   h->Lc = chain_levels(N);
   cudaGetDevice(&h->device);
-  h->pool_bytes = bm_workspace_bytes(desc);
-  if (cudaMalloc(&h->pool, h->pool_bytes) != cudaSuccess) {
+  h->pool_bytes = need;
+  if (mem) {
+    h->pool = mem;
+    h->owns_pool = false;
+  } else if (cudaMalloc(&h->pool, h->pool_bytes) != cudaSuccess) {
     cudaGetLastError();
     delete h;
     return BM_ERR_OOM;
   }
-  if (cudaMemset(h->pool, 0, kHeader) != cudaSuccess) goto cuda_fail;
+  if (light ? cudaMemsetAsync(h->pool, 0, kHeader, init_stream) != cudaSuccess
+            : cudaMemset(h->pool, 0, kHeader) != cudaSuccess)
+    goto cuda_fail;
   h->status = (Status *)h->pool;
   h->tickets = (unsigned *)((char *)h->pool + 256);
   if (desc->precision == BM_PREC_FP64) {
     char *p = (char *)h->pool + kHeader;
     const size_t SN = (size_t)S * N, b2 = (size_t)nb * nb;
-    auto take = [&](size_t bytes) {
+    auto take = [&](size_t nbytes) {
       double *q = (double *)p;
-      p += align_up(bytes, 256);
+      p += align_up(nbytes, 256);
       return q;
     };
     F64View &v = h->v;
@@ -152,21 +166,43 @@ extern "C" bm_status bm_analyze(const bm_desc *desc, void *stream, bm_handle *ou
   } else {
     if (mixed_prepare(nb, nr) != cudaSuccess) goto cuda_fail;
     h->mixed = mixed_create(S, N, nb, nr, (char *)h->pool + kHeader, h->pool_bytes - kHeader, h->status,
-                            h->tickets);
+                            h->tickets, light ? init_stream : nullptr, !light);
     if (!h->mixed) goto cuda_fail;
   }
-  if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) goto cuda_fail;
-  if (cudaDeviceSynchronize() != cudaSuccess) goto cuda_fail;
+  if (!light) {
+    if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) goto cuda_fail;
+    if (cudaDeviceSynchronize() != cudaSuccess) goto cuda_fail;
+  }
   *out = h;
   return BM_OK;
 cuda_fail:
   cudaGetLastError();
   if (h->mixed) mixed_destroy(h->mixed);
   if (h->cap) cudaStreamDestroy(h->cap);
-  cudaFree(h->pool);
+  if (h->owns_pool) cudaFree(h->pool);
   delete h;
   return BM_ERR_CUDA;
 }
+
+extern "C" bm_status bm_analyze(const bm_desc *desc, void *stream, bm_handle *out) {
+  (void)stream;
+  return analyze_impl(desc, nullptr, 0, nullptr, false, out);
+}
+
+// Releases a handle built by analyze_impl without synchronizing the device
+// (the caller guarantees its work has finished).
+void release_impl(bm_handle h) {
+  if (!h) return;
+  if (h->gfac.exec) cudaGraphExecDestroy(h->gfac.exec);
+  if (h->gsol.exec) cudaGraphExecDestroy(h->gsol.exec);
+  if (h->mixed) mixed_destroy(h->mixed);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->sD) cudaFree(h->sD);
+  if (h->owns_pool) cudaFree(h->pool);
+  delete h;
+}
+
+Status *handle_status(bm_handle h) { return h->status; }
 
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
@@ -346,12 +382,6 @@ extern "C" bm_status bm_factor_solve_host(bm_handle h, const double *hD, const d
 extern "C" void bm_destroy(bm_handle h) {
   if (!h) return;
   cudaDeviceSynchronize();
-  if (h->gfac.exec) cudaGraphExecDestroy(h->gfac.exec);
-  if (h->gsol.exec) cudaGraphExecDestroy(h->gsol.exec);
-  if (h->mixed) mixed_destroy(h->mixed);
-  if (h->cap) cudaStreamDestroy(h->cap);
-  if (h->sD) cudaFree(h->sD);
-  cudaFree(h->pool);
+  release_impl(h);
   cudaGetLastError();
-  delete h;
 }

@@ -478,6 +478,11 @@ void f64_cluster_launch_solve(const F64View &v, const double *r, double *x, doub
 cudaError_t f64_prepare(int nb, int nr) {
   (void)nb;
   (void)nr;
+  static bool done[64] = {false};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorUnknown;
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  if (dev >= 0 && dev < 64) done[dev] = true;   // attributes below are idempotent
   nb = nr = 64;
   const int smem = (int)f64_factor_smem(nb, nr);
   cudaError_t e = cudaFuncSetAttribute(k_factor_level, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

@@ -271,7 +271,7 @@ cudaError_t mixed_prepare(int nb, int nr) {
 }
 
 MixedState *mixed_create(int S, int N, int nb, int nr, void *base, size_t bytes, Status *status,
-                         unsigned *tickets) {
+                         unsigned *tickets, cudaStream_t init_stream, bool sync_init) {
   if (bytes < mixed_bytes(S, N, nb, nr)) return nullptr;
   MixedState *m = new (std::nothrow) MixedState();
   if (!m) return nullptr;
@@ -293,7 +293,8 @@ MixedState *mixed_create(int S, int N, int nb, int nr, void *base, size_t bytes,
   m->ctl = (IRCtl *)take(sizeof(IRCtl));
   m->status = status;
   m->tickets = tickets;
-  if (cudaMemset(m->ctl, 0, sizeof(IRCtl)) != cudaSuccess) {
+  if ((sync_init ? cudaMemset(m->ctl, 0, sizeof(IRCtl)) : cudaMemsetAsync(m->ctl, 0, sizeof(IRCtl), init_stream)) !=
+      cudaSuccess) {
     delete m;
     return nullptr;
   }
