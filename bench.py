@@ -282,12 +282,14 @@ def run_batched(args):
     batch.close()
     # the plain FP64 path on the same systems, one handle per system, back to back
     fp64_ms = None
+    fwd_max = None
     if not args.no_fp64_compare:
         # one system at a time (a handle per system would not fit beside the
         # batch): factor + solve timed with events after a warm-up, summed
         fp64_ms = 0.0
+        fwd_max = 0.0
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        for (S, N, nb, nr), d in zip(shapes, systems):
+        for (S, N, nb, nr), d, xb in zip(shapes, systems, xs):
             hnd = bm.BranchKKTSolver(S, N, nb, nr)
             x64 = torch.empty_like(d["r"])
             hnd.factor(d["D"], d["E"], d["C"], d["R"])
@@ -299,6 +301,7 @@ def run_batched(args):
             b.record(stream)
             torch.cuda.synchronize()
             fp64_ms += a.elapsed_time(b)
+            fwd_max = max(fwd_max, float((xb - x64).abs().max() / x64.abs().max()))
             hnd.close()
             del x64
     ms = fac + sol
@@ -311,6 +314,7 @@ def run_batched(args):
         "factor_ms": fac, "solve_ms": sol, "fp64_sequential_ms": fp64_ms,
         "speedup_vs_fp64_sequential": (fp64_ms / ms) if fp64_ms else None,
         "backward_error_max": max(etas), "failed_systems": len(bad), "schedule": sched,
+        "forward_error_vs_fp64_max": fwd_max if fp64_ms is not None else None,
         "autotune_s": tune_s, "generate_s": gen_s, "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -335,7 +339,8 @@ def run_serving(args):
     factored once and solved for 4 right-hand sides against its resident
     factor. The requests go through the library's serving runtime (admission
     by an HBM budget, one stream per slot), first with the FP32-tail +
-    refinement path, then with the plain FP64 path, on the same arrival
+    refinement path (a request it cannot resolve is re-run in FP64 by the
+    server), then with the plain FP64 path, on the same arrival
     trace; then both again at half the throughput the first run sustained.
     The inputs of a request are drawn from a pool of distinct systems and are
     resident in HBM before the stream starts; latency = completion of the
@@ -385,7 +390,7 @@ def run_serving(args):
 
     def one_run(precision, rate):
         server = bm.BranchKKTServer(budget, slots=args.slots, precision=precision, max_refine=args.max_refine,
-                                    tol=args.tol)
+                                    tol=args.tol, fp64_fallback=(precision == bm.BM_PREC_FP32_IR))
 
         def submit(rid, k, x):
             d = pool[k]
@@ -437,7 +442,8 @@ def run_serving(args):
                 "gflops": sum(flops) / span_s / 1e9, "p50_ms": _percentile(lat, 0.5), "p99_ms": _percentile(lat, 0.99),
                 "max_ms": max(lat), "makespan_s": span_s, "wall_s": wall, "failed": bad,
                 "device_backward_error_max": max(etas) if etas else None, "sample_backward_error_max": sample_eta,
-                "peak_arena_gb": stats["peak_bytes_in_use"] / 2 ** 30, "clocks": clocks}
+                "peak_arena_gb": stats["peak_bytes_in_use"] / 2 ** 30, "fp64_fallbacks": stats["fallbacks"],
+                "clocks": clocks}
 
     runs = {}
     runs["fp32ir"] = one_run(bm.BM_PREC_FP32_IR, args.rate)
@@ -562,6 +568,15 @@ def run_gpu(args):
     d2h = xh.numel() * 8
 
     eta, rel2 = gpu_backward_error(g, x)
+    fwd_vs_fp64 = None
+    if args.precision != "fp64":
+        # the error of the mixed result against the FP64 path's solution
+        ref = bm.BranchKKTSolver(w.S, w.N, w.nb, w.nr)
+        ref.factor(g["D"], g["E"], g["C"], g["R"])
+        x64 = ref.solve(g["r"])
+        fwd_vs_fp64 = float((x - x64).abs().max() / x64.abs().max())
+        ref.close()
+        del x64
     Lc = (w.N - 1).bit_length() if w.N > 1 else 0
     launches_per_step = solver.launches_per_step()
     fmean = statistics.mean(fac_ms)
@@ -578,6 +593,7 @@ def run_gpu(args):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "factor_us": fmean * 1e3, "solve_us": statistics.mean(sol_ms) * 1e3,
         "us_per_kkt": ms_per_step * 1e3, "backward_error": eta, "rel_residual": rel2,
+        "forward_error_vs_fp64": fwd_vs_fp64, "refinement_steps": info.get("iters"),
         "device_status": info["name"],
         "flops_per_kkt": {"method": fl["total"], "natural_order_factor": bmgen.natural_flops(w.S, w.N, w.nb, w.nr)},
         "roofline": {"kernel": "factor pipeline (k_factor_level x %d + k_factor_x1 + k_factor_root, one graph)" % Lc,
@@ -621,6 +637,7 @@ def run_gpu(args):
         line["fp32ir_same_workload"] = {
             "us_per_kkt": mms * 1e3, "value": world * fl["total"] / (mms * 1e-3) / 1e9, "unit": "GFLOP/s",
             "steps": k, "backward_error": meta, "rel_residual": mrel, "refinement_steps": minfo["iters"],
+            "forward_error_vs_fp64": float((xm - x).abs().max() / x.abs().max()),
             "device_status": minfo["name"], "speedup_vs_fp64": ms_per_step / mms}
         mixed.close()
     if dist:

@@ -301,11 +301,20 @@ typedef struct bm_server_s *bm_server;
  * them through its arena and copies x back before the request completes. */
 #define BM_REQ_HOST_IO 1
 
+/* bm_server_desc.flags: a BM_PREC_FP32_IR request whose factor or
+ * refinement fails (BM_ERR_NOT_SPD or BM_ERR_NOT_CONVERGED: the FP32 tail
+ * factor cannot resolve the system, e.g. when R - sum_i U_i cancels by more
+ * than FP32 tails can carry) is run again with BM_PREC_FP64, ahead of the
+ * queue, if its FP64 workspace fits the budget. The completion then reports
+ * the FP64 run's status and fallback = 1. */
+#define BM_SERVE_FP64_FALLBACK 1
+
 typedef struct {
   size_t hbm_budget; /* bytes of device memory for admitted requests (> 0) */
   int slots;         /* requests in flight at most, 1..BM_SERVE_MAX_SLOTS; one stream each */
   int precision;     /* bm_precision, for every request of the server */
   int max_refine;    /* as bm_desc.max_refine (mixed precision) */
+  int flags;         /* 0 or BM_SERVE_FP64_FALLBACK */
   double tol;        /* as bm_desc.tol */
 } bm_server_desc;
 
@@ -324,6 +333,7 @@ typedef struct {
   int status;            /* first non-OK status over factor and solves (bm_status) */
   int fail_scenario;     /* as bm_info, for BM_ERR_NOT_SPD */
   int fail_stage;
+  int fallback;          /* 1 if the result comes from the FP64 re-run (BM_SERVE_FP64_FALLBACK) */
   int iters[BM_SERVE_MAX_RHS];           /* refinement steps per right-hand side */
   double backward_error[BM_SERVE_MAX_RHS]; /* device estimate per rhs (mixed; -1 for FP64) */
   /* microseconds since bm_server_create: submission (host clock), start of
@@ -333,7 +343,7 @@ typedef struct {
 } bm_completion;
 
 typedef struct {
-  unsigned long long submitted, admitted, completed;
+  unsigned long long submitted, admitted, completed, fallbacks;
   int queued, in_flight;
   size_t bytes_in_use, peak_bytes_in_use, budget;
 } bm_server_stats;

@@ -33,6 +33,7 @@ BM_NOALLOC_SCRATCH_BYTES = 32 << 20
 BM_SERVE_MAX_RHS = 8
 BM_SERVE_MAX_SLOTS = 64
 BM_REQ_HOST_IO = 1
+BM_SERVE_FP64_FALLBACK = 1
 
 
 class bm_desc(ctypes.Structure):
@@ -48,7 +49,7 @@ class bm_info(ctypes.Structure):
 
 class bm_server_desc(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("slots", ctypes.c_int), ("precision", ctypes.c_int),
-                ("max_refine", ctypes.c_int), ("tol", ctypes.c_double)]
+                ("max_refine", ctypes.c_int), ("flags", ctypes.c_int), ("tol", ctypes.c_double)]
 
 
 class bm_request(ctypes.Structure):
@@ -60,14 +61,15 @@ class bm_request(ctypes.Structure):
 
 class bm_completion(ctypes.Structure):
     _fields_ = [("id", ctypes.c_ulonglong), ("status", ctypes.c_int), ("fail_scenario", ctypes.c_int),
-                ("fail_stage", ctypes.c_int), ("iters", ctypes.c_int * BM_SERVE_MAX_RHS),
+                ("fail_stage", ctypes.c_int), ("fallback", ctypes.c_int), ("iters", ctypes.c_int * BM_SERVE_MAX_RHS),
                 ("backward_error", ctypes.c_double * BM_SERVE_MAX_RHS), ("t_submit_us", ctypes.c_double),
                 ("t_start_us", ctypes.c_double), ("t_factor_us", ctypes.c_double), ("t_done_us", ctypes.c_double)]
 
 
 class bm_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_ulonglong), ("admitted", ctypes.c_ulonglong),
-                ("completed", ctypes.c_ulonglong), ("queued", ctypes.c_int), ("in_flight", ctypes.c_int),
+                ("completed", ctypes.c_ulonglong), ("fallbacks", ctypes.c_ulonglong), ("queued", ctypes.c_int),
+                ("in_flight", ctypes.c_int),
                 ("bytes_in_use", ctypes.c_size_t), ("peak_bytes_in_use", ctypes.c_size_t),
                 ("budget", ctypes.c_size_t)]
 
@@ -435,8 +437,10 @@ class BranchKKTBatch:
 # --------------------------------------------------------------------------
 # Serving runtime (include/bm.h, "Serving runtime")
 
-def make_server_desc(hbm_budget, slots=8, precision=BM_PREC_FP32_IR, max_refine=10, tol=1e-10) -> bm_server_desc:
-    return bm_server_desc(int(hbm_budget), int(slots), int(precision), int(max_refine), float(tol))
+def make_server_desc(hbm_budget, slots=8, precision=BM_PREC_FP32_IR, max_refine=10, tol=1e-10,
+                     fp64_fallback=False) -> bm_server_desc:
+    return bm_server_desc(int(hbm_budget), int(slots), int(precision), int(max_refine),
+                          BM_SERVE_FP64_FALLBACK if fp64_fallback else 0, float(tol))
 
 
 def _request(rid, S, N, nb, nr, D, E, C, R, r, x, host_io):
@@ -463,7 +467,8 @@ def bm_server_submit(s, req: bm_request) -> None:
 
 def _completion_dict(c: bm_completion, nrhs: int) -> dict:
     return {"id": int(c.id), "status": int(c.status), "fail_scenario": int(c.fail_scenario),
-            "fail_stage": int(c.fail_stage), "iters": [int(c.iters[j]) for j in range(nrhs)],
+            "fail_stage": int(c.fail_stage), "fallback": int(c.fallback),
+            "iters": [int(c.iters[j]) for j in range(nrhs)],
             "backward_error": [float(c.backward_error[j]) for j in range(nrhs)],
             "t_submit_us": float(c.t_submit_us), "t_start_us": float(c.t_start_us),
             "t_factor_us": float(c.t_factor_us), "t_done_us": float(c.t_done_us)}
@@ -493,8 +498,9 @@ class BranchKKTServer:
     Tensors of a request are held here until its completion is returned.
     """
 
-    def __init__(self, hbm_budget, slots=8, precision=BM_PREC_FP32_IR, max_refine=10, tol=1e-10):
-        self.desc = make_server_desc(hbm_budget, slots, precision, max_refine, tol)
+    def __init__(self, hbm_budget, slots=8, precision=BM_PREC_FP32_IR, max_refine=10, tol=1e-10,
+                 fp64_fallback=False):
+        self.desc = make_server_desc(hbm_budget, slots, precision, max_refine, tol, fp64_fallback)
         self.h = bm_server_create(self.desc)
         self._held = {}
 

@@ -75,6 +75,9 @@ struct Pending {
   bm_request req;
   double t_submit_us;
   size_t bytes;
+  int precision;          // of this attempt
+  int fallback;           // 1 for the FP64 re-run of a failed mixed attempt
+  double t_first_start_us;
 };
 
 // One stream slot. hs[0] receives the status word after the factor, hs[1+j]
@@ -97,10 +100,10 @@ struct IoLayout {
 
 // Offsets (relative to the request's arena range) of the factor workspace
 // and, under BM_REQ_HOST_IO, of the staged inputs and outputs.
-bool layout_of(const bm_server_desc &sd, const bm_request &q, IoLayout *L) {
+bool layout_of(const bm_server_desc &sd, int precision, const bm_request &q, IoLayout *L) {
   bm_desc d{};
   d.S = q.S; d.N = q.N; d.nb = q.nb; d.nr = q.nr;
-  d.precision = sd.precision;
+  d.precision = precision;
   d.max_refine = sd.max_refine;
   d.tol = sd.tol;
   const size_t work = bm_workspace_bytes(&d);
@@ -162,13 +165,14 @@ struct bm_server_s {
 extern "C" size_t bm_server_request_bytes(const bm_server_desc *desc, const bm_request *req) {
   if (!desc || !valid_request(*desc, req)) return 0;
   IoLayout L;
-  if (!layout_of(*desc, *req, &L)) return 0;
+  if (!layout_of(*desc, desc->precision, *req, &L)) return 0;
   return L.total;
 }
 
 static bool valid_server_desc(const bm_server_desc *d) {
   if (!d || d->hbm_budget < kAlign) return false;
   if (d->slots < 1 || d->slots > BM_SERVE_MAX_SLOTS) return false;
+  if (d->flags & ~BM_SERVE_FP64_FALLBACK) return false;
   return d->precision == BM_PREC_FP64 || d->precision == BM_PREC_FP32_IR;
 }
 
@@ -240,10 +244,10 @@ static bm_status launch_request(bm_server s, Slot &sl) {
   cudaStream_t st = sl.stream;
   char *base = s->arena_base + sl.off;
   IoLayout L;
-  layout_of(sd, q, &L);
+  layout_of(sd, sl.job.precision, q, &L);
   bm_desc d{};
   d.S = q.S; d.N = q.N; d.nb = q.nb; d.nr = q.nr;
-  d.precision = sd.precision;
+  d.precision = sl.job.precision;
   d.max_refine = sd.max_refine;
   d.tol = sd.tol;
   d.flags = BM_FLAG_NO_GRAPH;
@@ -300,8 +304,9 @@ static void retire(bm_server s, Slot &sl, bm_status launch_rc) {
   bm_completion c{};
   c.id = sl.job.req.id;
   c.t_submit_us = sl.job.t_submit_us;
+  c.fallback = sl.job.fallback;
   const int nrhs = sl.job.req.nrhs;
-  const bool mixed = s->desc.precision == BM_PREC_FP32_IR;
+  const bool mixed = sl.job.precision == BM_PREC_FP32_IR;
   if (launch_rc != BM_OK) {
     c.status = launch_rc;
     c.t_start_us = c.t_factor_us = c.t_done_us = -1.0;
@@ -332,6 +337,22 @@ static void retire(bm_server s, Slot &sl, bm_status launch_rc) {
   s->arena->release(sl.off, sl.job.bytes);
   sl.busy = false;
   s->stats.in_flight--;
+  if (sl.job.fallback) c.t_start_us = sl.job.t_first_start_us;
+  // a mixed attempt that the FP32 tails could not resolve runs again in FP64
+  IoLayout L64;
+  if (mixed && (s->desc.flags & BM_SERVE_FP64_FALLBACK) && launch_rc == BM_OK &&
+      (c.status == BM_ERR_NOT_SPD || c.status == BM_ERR_NOT_CONVERGED) &&
+      layout_of(s->desc, BM_PREC_FP64, sl.job.req, &L64) && L64.total <= s->arena->capacity()) {
+    Pending p = sl.job;
+    p.precision = BM_PREC_FP64;
+    p.fallback = 1;
+    p.bytes = L64.total;
+    p.t_first_start_us = c.t_start_us;
+    s->queue.push_front(p);
+    s->stats.queued++;
+    s->stats.fallbacks++;
+    return;
+  }
   s->stats.completed++;
   s->done.push_back(c);
 }
@@ -388,11 +409,12 @@ static bm_status advance(bm_server s) {
 extern "C" bm_status bm_server_submit(bm_server s, const bm_request *req) {
   if (!s || !valid_request(s->desc, req)) return BM_ERR_INVALID_ARG;
   IoLayout L;
-  if (!layout_of(s->desc, *req, &L) || L.total > s->arena->capacity()) return BM_ERR_INVALID_ARG;
-  Pending p;
+  if (!layout_of(s->desc, s->desc.precision, *req, &L) || L.total > s->arena->capacity()) return BM_ERR_INVALID_ARG;
+  Pending p{};
   p.req = *req;
   p.t_submit_us = now_us(s->t0);
   p.bytes = L.total;
+  p.precision = s->desc.precision;
   s->queue.push_back(p);
   s->stats.submitted++;
   s->stats.queued++;

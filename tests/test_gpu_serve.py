@@ -222,3 +222,35 @@ def test_failing_request_is_isolated():
         if i != bad:
             assert by_id[i]["status"] == 0
             assert np.array_equal(mixed[i], alone[i])
+
+
+def test_mixed_failure_falls_back_to_fp64():
+    """A root Schur complement R - sum_i U_i that cancels to 1e-9 of R0: FP64
+    resolves it, FP32 tails cannot. Without the fallback flag the mixed
+    request reports its failure; with it, the server re-runs the request in
+    FP64 and returns exactly the FP64 result."""
+    bm = _bm()
+    reqs = make_requests([(6, 24, 12, 4), (3, 17, 6, 2)], seed0=130)
+    d = reqs[0]
+    d["R"] = (d["R"] - (1.0 - 1e-9) * d["R0"]).contiguous()
+    fp64_x, fp64_c = run_alone(reqs, bm.BM_PREC_FP64)
+    assert all(c["status"] == 0 for c in fp64_c)
+    res = natural.residual(d["D"], d["E"], d["C"], d["R"], fp64_x[0][0], d["rs"][0])
+    assert res["eta"] <= 1e-12
+    _, plain, _ = run_mix(reqs, bm.BM_PREC_FP32_IR, tol=1e-12)
+    by_id = {c["id"]: c for c in plain}
+    assert by_id[0]["status"] in (2, 5) and by_id[0]["fallback"] == 0, by_id[0]
+    assert by_id[1]["status"] == 0
+    server = bm.BranchKKTServer(2 << 30, slots=4, precision=bm.BM_PREC_FP32_IR, tol=1e-12, fp64_fallback=True)
+    gs = [to_dev(q) for q in reqs]
+    xs = [torch.empty_like(g["rs"]) for g in gs]
+    for i, g in enumerate(gs):
+        submit(server, i, g, xs[i])
+    comps = {c["id"]: c for c in server.drain()}
+    st = server.stats()
+    server.close()
+    assert comps[0]["status"] == 0 and comps[0]["fallback"] == 1, comps[0]
+    assert comps[1]["status"] == 0 and comps[1]["fallback"] == 0
+    assert st["fallbacks"] == 1 and st["completed"] == 2
+    assert np.array_equal(xs[0].cpu().numpy(), fp64_x[0])
+    assert comps[0]["t_start_us"] <= comps[0]["t_factor_us"] <= comps[0]["t_done_us"]
