@@ -57,6 +57,30 @@ def fp64_peak_gflops(sm_mhz=None):
     return 152 * 2 * 2 * mhz * 1e6 / 1e9
 
 
+def fp32_peak_gflops(sm_mhz=None):
+    """FP32 ALU peak: 152 SMs x 128 FMA lanes per clock x 2 flop x the
+    maximum SM clock (121 lane-ops per SM per clock measured with FFMA)."""
+    peaks, _ = _peaks()
+    mhz = sm_mhz or peaks.get("sm_max_mhz", 2070.0)
+    return 152 * 128 * 2 * mhz * 1e6 / 1e9
+
+
+def _factor_kernels(N, nb, precision):
+    """Names of the kernels one factor launches (one CUDA graph)."""
+    Lc = (N - 1).bit_length() if N > 1 else 0
+    top = Lc
+    for lvl in range(Lc):
+        if (N // 2 if lvl == 0 else ((N - 1) >> lvl) + 1) <= 4:
+            top = lvl
+            break
+    if precision == "fp64":
+        if nb in (2, 3, 4, 6, 8, 12, 16, 24, 32, 48):
+            return "k_factor_level_team x%d + k_factor_top + k_factor_root" % top
+        return "k_factor_level x%d + k_factor_x1 + k_factor_root" % Lc
+    suffix = "" if nb <= 32 else "_w"
+    return "k_level_rows%s x%d + k_top_rows%s + k_factor_root" % (suffix, top, suffix)
+
+
 def _kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2609_29977_gb300", "csrc")
@@ -141,6 +165,24 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def max_over_ranks(value, dist=None, device="cpu"):
+    """The largest per-rank value over all ranks (the slowest replica sets
+    the whole-job time); the value itself without a process group."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gflops(world, flops_per_step, steps, slowest_ms):
+    """Whole-job throughput: every rank solves its own replica (weak
+    scaling), so the job does world x steps systems in the slowest rank's
+    time."""
+    return world * flops_per_step * steps / (slowest_ms * 1e-3) / 1e9
 
 
 def time_oracle(sysd, budget_s, min_reps=3, nthreads=0):
@@ -538,12 +580,9 @@ def run_gpu(args):
     sol_ms = [b.elapsed_time(c) for _, b, c in ev]
     tot_ms = sum(f + s for f, s in zip(fac_ms, sol_ms))
     info = solver.query()
-    if dist:
-        t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = max_over_ranks(tot_ms, dist, dev)
     ms_per_step = tot_ms / args.steps
-    value = world * fl["total"] * args.steps / (tot_ms * 1e-3) / 1e9
+    value = whole_job_gflops(world, fl["total"], args.steps, tot_ms)
 
     # end to end through the public host-buffer entry point (pinned memory)
     pin = {k: sysd[k].contiguous().pin_memory() for k in ("D", "E", "C", "R", "r")}
@@ -559,11 +598,7 @@ def run_gpu(args):
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
         if code != 0:
             raise RuntimeError("host entry status %d" % code)
-    e2e_step = statistics.mean(e2e_ms)
-    if dist:
-        t = torch.tensor([e2e_step], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_step = float(t.item())
+    e2e_step = max_over_ranks(statistics.mean(e2e_ms), dist, dev)
     h2d = sum(pin[k].numel() * 8 for k in ("D", "E", "C", "R", "r"))
     d2h = xh.numel() * 8
 
@@ -577,10 +612,15 @@ def run_gpu(args):
         fwd_vs_fp64 = float((x - x64).abs().max() / x64.abs().max())
         ref.close()
         del x64
-    Lc = (w.N - 1).bit_length() if w.N > 1 else 0
     launches_per_step = solver.launches_per_step()
     fmean = statistics.mean(fac_ms)
-    peak_alu = fp64_peak_gflops()
+    mhz = _peaks()[0].get("sm_max_mhz", 2070.0)
+    if args.precision == "fp64":
+        peak_alu = fp64_peak_gflops()
+        peak_src = "FP64 ALU derived: 152 SMs x 2 FMA/clk x 2 flop x %.0f MHz" % mhz
+    else:
+        peak_alu = fp32_peak_gflops()
+        peak_src = "FP32 ALU derived: 152 SMs x 128 FMA/clk x 2 flop x %.0f MHz (tails are FP32)" % mhz
     achieved = fl["factor"] / (fmean * 1e-3) / 1e9
     traffic = _profile_traffic(w.name, args.precision)
     line = {
@@ -596,12 +636,12 @@ def run_gpu(args):
         "forward_error_vs_fp64": fwd_vs_fp64, "refinement_steps": info.get("iters"),
         "device_status": info["name"],
         "flops_per_kkt": {"method": fl["total"], "natural_order_factor": bmgen.natural_flops(w.S, w.N, w.nb, w.nr)},
-        "roofline": {"kernel": "factor pipeline (k_factor_level x %d + k_factor_x1 + k_factor_root, one graph)" % Lc,
+        "roofline": {"kernel": "factor pipeline (%s, one graph)" % _factor_kernels(w.N, w.nb, args.precision),
                      "bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "GFLOP/s",
-                     "frac": achieved / peak_alu, "traffic": traffic,
-                     "peak_source": "FP64 ALU derived: 152 SMs x 2 FMA/clk x 2 flop x %.0f MHz" %
-                                    _peaks()[0].get("sm_max_mhz", 2070.0)},
-        "e2e": {"value": world * fl["total"] / (e2e_step * 1e-3) / 1e9, "unit": "GFLOP/s",
+                     "frac": achieved / peak_alu, "traffic": traffic, "peak_source": peak_src,
+                     "achieved_basis": "method flops of one factor (%.4g) / mean factor time over the timed "
+                                       "steps (CUDA events on the launching stream)" % fl["factor"]},
+        "e2e": {"value": whole_job_gflops(world, fl["total"], 1, e2e_step), "unit": "GFLOP/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,

@@ -77,11 +77,20 @@ __device__ inline double root_sum(const double *U, int S, int nr, int i, int j) 
   double a[4] = {0.0, 0.0, 0.0, 0.0};
   const size_t stride = (size_t)nr * nr, off = (size_t)i * nr + j;
   int s = 0;
+  // sixteen loads in flight per step; accumulator k still adds U[s + k],
+  // U[s + 4 + k], ... in increasing s, so the bits do not depend on the unroll
+  for (; s + 16 <= S; s += 16) {
+    double v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = __ldcg(U + (size_t)(s + k) * stride + off);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) a[k & 3] += v[k];
+  }
   for (; s + 4 <= S; s += 4) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) a[k] += U[(size_t)(s + k) * stride + off];
+    for (int k = 0; k < 4; ++k) a[k] += __ldcg(U + (size_t)(s + k) * stride + off);
   }
-  for (int k = 0; s < S; ++s, ++k) a[k] += U[(size_t)s * stride + off];
+  for (int k = 0; s < S; ++s, ++k) a[k] += __ldcg(U + (size_t)s * stride + off);
   return (a[0] + a[1]) + (a[2] + a[3]);
 }
 
