@@ -72,7 +72,7 @@ typedef struct {
   int S, N, nb, nr;   /* scenarios (the paper's M), horizon, stage block, root block */
   int precision;      /* bm_precision */
   int max_refine;     /* BM_PREC_FP32_IR: maximum refinement steps (<= 0: 10) */
-  double tol;         /* BM_PREC_FP32_IR: target normwise backward error (<= 0: 1e-10) */
+  double tol;         /* BM_PREC_FP32_IR: target componentwise backward error (<= 0: 1e-10), see bm_solve */
   unsigned flags;     /* BM_FLAG_* */
 } bm_desc;
 
@@ -81,7 +81,7 @@ typedef struct {
   int fail_scenario;   /* BM_ERR_NOT_SPD: 0-based scenario, -1 for the root */
   int fail_stage;      /* BM_ERR_NOT_SPD: 1-based stage k of that tail, 0 for the root */
   int iters;           /* BM_PREC_FP32_IR: refinement steps of the last solve */
-  double backward_error; /* BM_PREC_FP32_IR: eta of the last solve; FP64: -1 */
+  double backward_error; /* BM_PREC_FP32_IR: componentwise backward error of the returned x; FP64: -1 */
 } bm_info;
 
 /* Library version (BM_VERSION). */
@@ -128,8 +128,11 @@ bm_status bm_factor(bm_handle h, const double *D, const double *E, const double 
  * backward substitution and the inverse permutation. r and x are device
  * vectors of length S*N*nb + nr in natural order; x must not alias r.
  * BM_PREC_FP32_IR: iterative refinement on K with an FP64 residual until
- * the backward error is <= tol or max_refine steps (status
- * BM_ERR_NOT_CONVERGED then). Asynchronous.
+ * the componentwise backward error
+ *     omega = max_i |r - K x|_i / (|K| |x| + |r|)_i     (Oettli-Prager)
+ * is <= tol. It reports BM_ERR_NOT_CONVERGED (x = the last iterate) after
+ * max_refine corrections, or earlier once omega fails to halve from one
+ * correction to the next (stalled or diverging refinement). Asynchronous.
  * Errors: BM_ERR_INVALID_ARG, BM_ERR_NOT_FACTORED, BM_ERR_CUDA.
  */
 bm_status bm_solve(bm_handle h, const double *r, double *x, void *stream);
@@ -253,7 +256,8 @@ bm_status bm_batch_factor(bm_batch b, const double *const *D, const double *cons
 
 /*
  * Solves every system (Alg. 2 with FP32 tails and an FP64 root step, then
- * FP64 refinement until each system's backward error <= tol); r and x are
+ * FP64 refinement until each system's componentwise backward error <= tol,
+ * as for bm_solve); r and x are
  * DEVICE arrays of count device pointers. Asynchronous.
  */
 bm_status bm_batch_solve(bm_batch b, const double *const *r, double *const *x, void *stream);
@@ -335,7 +339,7 @@ typedef struct {
   int fail_stage;
   int fallback;          /* 1 if the result comes from the FP64 re-run (BM_SERVE_FP64_FALLBACK) */
   int iters[BM_SERVE_MAX_RHS];           /* refinement steps per right-hand side */
-  double backward_error[BM_SERVE_MAX_RHS]; /* device estimate per rhs (mixed; -1 for FP64) */
+  double backward_error[BM_SERVE_MAX_RHS]; /* componentwise, per rhs (mixed; -1 for FP64) */
   /* microseconds since bm_server_create: submission (host clock), start of
    * the request's first copy or kernel, end of its factor, end of its last
    * solve/copy (device event clock) */

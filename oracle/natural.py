@@ -88,9 +88,38 @@ def solve(fac: dict, r, nthreads: int = 0) -> np.ndarray:
     return x
 
 
+def abs_kx(D, E, C, R, x) -> np.ndarray:
+    """|K| |x| for the root-coupled matrix of Sec. III-B (Eq.
+    root_coupled_matrix): stage blocks D (lower triangles, mirrored),
+    sub-diagonal blocks E and their transposes, C_{s,1} coupling stage 1 of
+    tail s to the root, root block R; written out block by block."""
+    D, E, C, R, x = (_f64(a) for a in (D, E, C, R, x))
+    S, N, nb, _ = D.shape
+    nr = R.shape[0]
+    n0 = S * N * nb
+    X = np.abs(x[:n0]).reshape(S, N, nb)
+    x0 = np.abs(x[n0:])
+    Dl = np.tril(D)
+    Dfull = np.abs(Dl + np.swapaxes(np.tril(Dl, -1), -1, -2))
+    out = np.einsum("snij,snj->sni", Dfull, X)
+    if N > 1:
+        Ea = np.abs(E)
+        out[:, 1:] += np.einsum("snij,snj->sni", Ea, X[:, :-1])     # block (k+1, k) = E_k
+        out[:, :-1] += np.einsum("snji,snj->sni", Ea, X[:, 1:])     # block (k, k+1) = E_k^T
+    Ca = np.abs(C)
+    out[:, 0] += np.einsum("sji,j->si", Ca, x0)                     # block (1, root) = C^T
+    Rl = np.tril(R)
+    Rfull = np.abs(Rl + np.tril(Rl, -1).T)
+    root = Rfull @ x0 + np.einsum("sij,sj->i", Ca, X[:, 0])
+    return np.concatenate([out.reshape(-1), root])
+
+
 def residual(D, E, C, R, x, r, nthreads: int = 0) -> dict:
-    """rho = r - K x in FP64 and the normwise backward error
-    eta = ||rho||_inf / (||K||_inf ||x||_inf + ||r||_inf)."""
+    """rho = r - K x in FP64, the normwise backward error
+    eta = ||rho||_inf / (||K||_inf ||x||_inf + ||r||_inf), the componentwise
+    (Oettli-Prager) backward error omega = max_i |rho_i| / (|K| |x| + |r|)_i
+    and the relative residuals ||rho||_inf / ||r||_inf (rel_inf) and
+    ||rho||_2 / ||r||_2."""
     D, E, C, R, x, r = (_f64(a) for a in (D, E, C, R, x, r))
     S, N, nb, _ = D.shape
     nr = R.shape[0]
@@ -100,7 +129,13 @@ def residual(D, E, C, R, x, r, nthreads: int = 0) -> dict:
     _load().bmo_residual(S, N, nb, nr, _p(D), _p(Ep), _p(C), _p(R), _p(x), _p(r), _p(rho), _p(out),
                          int(nthreads))
     eta = out[0] / (out[1] * out[2] + out[3])
-    return {"rho": rho, "eta": float(eta), "rel2": float(out[4] / out[5]), "K_inf": float(out[1])}
+    rel_inf = out[0] / out[3] if out[3] > 0 else (0.0 if out[0] == 0 else float("inf"))
+    den = abs_kx(D, E, C, R, x) + np.abs(r)
+    num = np.abs(rho)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ratio = np.where(den > 0, num / np.where(den > 0, den, 1.0), np.where(num > 0, np.inf, 0.0))
+    return {"rho": rho, "eta": float(eta), "rel2": float(out[4] / out[5]), "rel_inf": float(rel_inf),
+            "omega": float(ratio.max()), "K_inf": float(out[1])}
 
 
 def tail_schur_first(D, E, nthreads: int = 0) -> np.ndarray:

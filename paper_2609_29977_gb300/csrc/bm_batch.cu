@@ -248,8 +248,6 @@ __global__ void k_batch_prep(BInst *inst, int ninst, BClass *cls, int ncls) {
     if (threadIdx.x == 0) {
       *I.x1_done = 0u;
       memset(I.m.status, 0, sizeof(Status));
-      I.m.ctl->knorm_valid = 0;
-      I.m.ctl->kmax = 0ull;
       for (int k = 0; k < 4; ++k) I.m.tickets[k] = 0u;
     }
   }

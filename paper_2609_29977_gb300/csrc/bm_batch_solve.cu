@@ -8,16 +8,15 @@ namespace bm {
 namespace {
 using namespace mx;
 
-// Per-solve reset of the control blocks (keeps ||K|| of the factor).
+// Per-solve reset of the control blocks.
 __global__ void k_batch_reset(BInst *inst, int ninst) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= ninst) return;
   IRCtl *c = inst[b].m.ctl;
   c->converged = 0;
   c->iters = 0;
-  c->rmax = 0ull;
-  c->xmax = 0ull;
-  c->bmax = 0ull;
+  c->wmax = 0u;
+  c->omega_prev = 0.0;
   inst[b].m.tickets[2] = 0u;
   inst[b].m.tickets[3] = 0u;
 }
@@ -70,7 +69,7 @@ __global__ void __launch_bounds__(256) k_batch_res(const BInst *inst, const BTai
   switch (I.nb) {
 #define X(n)                                     \
   case n:                                        \
-    residual_tail<n>(I.m, r, x, t.s, iter);      \
+    residual_tail<n>(I.m, r, x, t.s);            \
     break;
     BM_BATCH_NB_LIST(X)
 #undef X

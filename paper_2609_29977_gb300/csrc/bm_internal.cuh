@@ -59,7 +59,7 @@ struct Status {
   int scenario;   // 0-based, -1 root
   int stage;      // 1-based natural stage, 0 root
   int iters;      // refinement steps
-  double eta;     // refinement backward error
+  double eta;     // refinement: componentwise backward error of the iterate
 };
 
 __device__ inline void report_not_spd(Status *st, int scenario, int stage) {

@@ -10,11 +10,13 @@
 // Solve: x_0 = 0, rho_0 = r; for k = 0..max_refine:
 //   d = M^{-1} rho_k  (Alg. 2 with FP32 tails and an FP64 root step),
 //   x += d (FP64), rho_{k+1} = r - K x (FP64, from the caller's D, E, C, R),
-//   eta = ||rho||_inf / (||K||_inf ||x||_inf + ||r||_inf); stop when eta <= tol.
+//   stop when the componentwise backward error
+//   omega = max_i |rho_i| / (|K| |x| + |r|)_i <= tol (Oettli-Prager), or
+//   when omega fails to halve from one iteration to the next.
 // Each iteration is three launches: forward tail substitution whose last CTA
 // does the root step, backward tail substitution fused with x += d, and the
-// residual whose last CTA evaluates eta and raises a device flag once
-// converged; every later launch checks the flag first and returns, so the
+// residual whose last CTA applies the stopping test and raises a device flag
+// once it holds; every later launch checks the flag first and returns, so the
 // whole unrolled loop is one CUDA graph with no host round trip.
 #include <cuda_runtime.h>
 
@@ -45,160 +47,37 @@ __global__ void __launch_bounds__(256) k_mixed_bwd(MixedState m, double *x, int 
   bwd_tail<NB>(m, x, iter, blockIdx.x / CS, (int)cluster_rank(), CS, sX);
 }
 
-// rho = r - K x in FP64 with the norms of the stopping test; one team of
-// NB lanes per (tail, stage) block row (row i of the block per lane), one
-// more CTA-strided pass over the root rows. The last CTA evaluates eta.
+// rho = r - K x in FP64 and the componentwise backward error of the
+// iterate; one team of NB lanes per (tail, stage) block row (row i of the
+// block per lane), one more CTA-strided pass over the root rows. The last
+// CTA applies the stopping test.
 template <int NB>
 __global__ void __launch_bounds__(256) k_mixed_residual(MixedState m, const double *__restrict__ r,
                                                          const double *__restrict__ x, int iter, int max_iter,
                                                          double tol) {
-  constexpr int TS = MCfg<NB>::TS, TEAMS = MCfg<NB>::TEAMS, NB2 = NB * NB;
-  __shared__ int last;
+  constexpr int TS = MCfg<NB>::TS, TEAMS = MCfg<NB>::TEAMS;
+  __shared__ unsigned sroot;
   const Team<TS> tm;
   pdl_wait();
   if (ir_done(m.ctl)) return;
-  const int N = m.N, S = m.S, nr = m.nr;
-  const size_t n0 = (size_t)S * N * NB;
-  const bool knorm = !m.ctl->knorm_valid;
-  const double *D = m.D, *E = m.E, *C = m.C, *R = m.R;
-  const double *x0 = x + n0;
-  unsigned long long rmax = 0, xmax = 0, bmax = 0;
-  float kmax = 0.0f;
-  const long nrow = (long)S * N;
-  const int i = tm.lane;
+  const long nrow = (long)m.S * m.N;
+  float om = 0.0f;
   for (long br = (long)blockIdx.x * TEAMS + tm.id; br < nrow; br += (long)gridDim.x * TEAMS) {
-    if (i >= NB) continue;
-    const int s = (int)(br / N), k = (int)(br - (long)s * N);
-    const size_t off = (size_t)br * NB;
-    const double *Dk = D + (size_t)br * NB2;
-    const double *xk = x + off;
-    double acc = r[off + i];
-    float ks = 0.0f;
-#pragma unroll
-    for (int j = 0; j < NB; ++j) {
-      const double kij = j <= i ? Dk[i * NB + j] : Dk[j * NB + i];
-      acc = fma(-kij, xk[j], acc);
-      if (knorm) ks += abs_f32_approx(kij);
-    }
-    if (k > 0) {   // block (k, k-1) = E_k (1-based stage k+1)
-      const double *Ek = E + ((size_t)s * (N - 1) + (k - 1)) * NB2 + i * NB;
-      const double *xp = xk - NB;
-#pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        acc = fma(-Ek[j], xp[j], acc);
-        if (knorm) ks += abs_f32_approx(Ek[j]);
-      }
-    }
-    if (k + 1 < N) {   // block (k, k+1) = E_{k+1}^T
-      const double *Ek = E + ((size_t)s * (N - 1) + k) * NB2 + i;
-      const double *xn = xk + NB;
-#pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        acc = fma(-Ek[j * NB], xn[j], acc);
-        if (knorm) ks += abs_f32_approx(Ek[j * NB]);
-      }
-    }
-    if (k == 0) {   // block (1, root) = C_s^T
-      const double *Cs = C + (size_t)s * nr * NB + i;
-      for (int j = 0; j < nr; ++j) {
-        acc = fma(-Cs[j * NB], x0[j], acc);
-        if (knorm) ks += abs_f32_approx(Cs[j * NB]);
-      }
-    }
-    m.rho[off + i] = acc;
-    const unsigned long long ra = abs_bits(acc), xa = abs_bits(xk[i]);
-    rmax = ra > rmax ? ra : rmax;
-    xmax = xa > xmax ? xa : xmax;
-    if (iter == 0) {
-      const unsigned long long ba = abs_bits(r[off + i]);
-      bmax = ba > bmax ? ba : bmax;
-    }
-    kmax = ks > kmax ? ks : kmax;
+    if (tm.lane >= NB) continue;
+    const int s = (int)(br / m.N), k = (int)(br - (long)s * m.N);
+    om = fmaxf(om, residual_row<NB>(m, r, x, s, k, tm.lane));
   }
-  // root rows: R x0 + sum_s C_s x_{s,1}, one component per CTA-strided row
-  for (int c = blockIdx.x; c < nr; c += gridDim.x) {
-    double acc = 0.0;
-    float ks = 0.0f;
-    for (long e = threadIdx.x; e < (long)S * NB + nr; e += blockDim.x) {
-      double kv, xv;
-      if (e < (long)S * NB) {
-        const int s = (int)(e / NB), j = (int)(e - (long)s * NB);
-        kv = C[((size_t)s * nr + c) * NB + j];
-        xv = x[(size_t)s * N * NB + j];
-      } else {
-        const int j = (int)(e - (long)S * NB);
-        kv = j <= c ? R[c * nr + j] : R[j * nr + c];
-        xv = x0[j];
-      }
-      acc = fma(kv, xv, acc);
-      if (knorm) ks += abs_f32_approx(kv);
-    }
-    __shared__ double red[256];
-    __shared__ float redf[256];
-    red[threadIdx.x] = acc;
-    redf[threadIdx.x] = ks;
-    for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
-      __syncthreads();
-      if ((int)threadIdx.x < w) {
-        red[threadIdx.x] += red[threadIdx.x + w];
-        redf[threadIdx.x] += redf[threadIdx.x + w];
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const double rc = r[n0 + c] - red[0];
-      m.rho[n0 + c] = rc;
-      const unsigned long long ra = abs_bits(rc), xa = abs_bits(x0[c]);
-      rmax = ra > rmax ? ra : rmax;
-      xmax = xa > xmax ? xa : xmax;
-      if (iter == 0) {
-        const unsigned long long ba = abs_bits(r[n0 + c]);
-        bmax = ba > bmax ? ba : bmax;
-      }
-      kmax = redf[0] > kmax ? redf[0] : kmax;
-    }
-    __syncthreads();
-  }
-  rmax = warp_max_u64(rmax);
-  xmax = warp_max_u64(xmax);
-  bmax = warp_max_u64(bmax);
-  unsigned kb = __float_as_uint(kmax);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned w = __shfl_xor_sync(0xffffffffu, kb, o);
-    kb = w > kb ? w : kb;
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicMax(&m.ctl->rmax, rmax);
-    atomicMax(&m.ctl->xmax, xmax);
-    if (iter == 0) atomicMax(&m.ctl->bmax, bmax);
-    if (knorm) atomicMax(&m.ctl->kmax, (unsigned long long)kb);
-  }
-  __threadfence();
+  omega_publish(m.ctl, om);
+  // root rows; their omega goes through the same maximum
+  if (threadIdx.x == 0) sroot = 0u;
   __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(&m.tickets[3], 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (!last || threadIdx.x != 0) return;
-  __threadfence();
-  IRCtl *ctl = m.ctl;
-  const double rn = __longlong_as_double((long long)atomicAdd(&ctl->rmax, 0ull));
-  const double xn = __longlong_as_double((long long)atomicAdd(&ctl->xmax, 0ull));
-  const double bn = __longlong_as_double((long long)atomicAdd(&ctl->bmax, 0ull));
-  const double kn = (double)__uint_as_float((unsigned)atomicAdd(&ctl->kmax, 0ull));
-  const double eta = rn / (kn * xn + bn);
-  ctl->eta = eta;
-  ctl->iters = iter;
-  ctl->knorm_valid = 1;
-  m.status->eta = eta;
-  m.status->iters = iter;
-  if (eta <= tol) {
-    ctl->converged = 1;
-  } else if (iter >= max_iter && m.status->code == 0) {
-    m.status->code = (int)BM_ERR_NOT_CONVERGED;
+  for (int c = blockIdx.x; c < m.nr; c += gridDim.x) {
+    const float oc = residual_root_row(m, r, x, NB, c);
+    if (threadIdx.x == 0) sroot = max(sroot, __float_as_uint(oc));
   }
-  ctl->rmax = 0ull;
-  ctl->xmax = 0ull;
-  m.tickets[3] = 0u;
+  __syncthreads();
+  if (threadIdx.x == 0 && sroot) atomicMax(&m.ctl->wmax, sroot);
+  if (last_cta(&m.tickets[3], gridDim.x) && threadIdx.x == 0) ir_stop(m, 0.0f, iter, max_iter, tol);
 }
 
 // Widen the FP32 tail factor for export.
@@ -315,17 +194,13 @@ void mixed_launch_factor(MixedState *m, const double *D, const double *E, const 
   t.D = D; t.E = E; t.C = C; t.R = R;
   t.Ld = m->Ld; t.Ll = m->Ll; t.Lr = m->Lr; t.Dt = m->Dt; t.W = m->W; t.invd = m->invd;
   t.F = m->F; t.U = m->U; t.status = m->status;
-  cudaMemsetAsync(&m->ctl->knorm_valid, 0, sizeof(int), st);
-  cudaMemsetAsync(&m->ctl->kmax, 0, sizeof(unsigned long long), st);
   tail_factor_launch<float>(t, st);
   f64_launch_factor_root_raw(m->S, m->nr, m->U, R, m->Rt, m->LR, m->tickets, m->status, st);
 }
 
 void mixed_launch_solve(MixedState *m, const double *r, double *x, int max_refine, double tol, cudaStream_t st) {
-  // reset the per-solve control words (keep ||K|| of the factor)
-  cudaMemsetAsync(&m->ctl->converged, 0, 2 * sizeof(int), st);
-  cudaMemsetAsync(&m->ctl->rmax, 0, 2 * sizeof(unsigned long long), st);
-  cudaMemsetAsync(&m->ctl->bmax, 0, sizeof(unsigned long long), st);
+  // reset the per-solve control words
+  cudaMemsetAsync(m->ctl, 0, sizeof(IRCtl), st);
   for (int it = 0; it <= max_refine; ++it) {
     switch (m->nb) {
 #define X(n)                                                  \

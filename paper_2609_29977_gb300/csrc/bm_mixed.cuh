@@ -7,13 +7,12 @@
 namespace bm {
 
 struct IRCtl {
-  int converged;                  // set by the residual kernel once eta <= tol
-  int iters;                      // corrections applied in the last solve
-  unsigned long long rmax, xmax;  // |rho|_inf, |x|_inf of the running iteration (bit patterns)
-  unsigned long long kmax, bmax;  // ||K||_inf (computed once per factor), ||r||_inf (once per solve)
-  int knorm_valid;
+  int converged;            // stop flag: the stopping test held, or refinement stalled
+  int iters;                // corrections applied in the last solve
+  unsigned wmax;            // max_i omega_i of the running iteration (bits of a non-negative float)
   int pad;
-  double eta;
+  double omega_prev;        // omega after the previous iteration
+  double eta;               // omega after the last iteration
 };
 
 struct MixedState {
@@ -306,169 +305,168 @@ __device__ __forceinline__ void bwd_tail(const MixedState &m, double *x, int ite
 
 
 
-// rho = r - K x for the rows of tail s (FP64) with the norms of the stopping
-// test accumulated into the system's control block (one CTA per tail).
-template <int NB>
-__device__ __forceinline__ void residual_tail(const MixedState &m, const double *__restrict__ r,
-                                              const double *__restrict__ x, int s, int iter) {
-  constexpr int TS = MCfg<NB>::TS, TEAMS = MCfg<NB>::TEAMS, NB2 = NB * NB;
-  const Team<TS> tm;
-  const int N = m.N, nr = m.nr, S = m.S;
-  const size_t n0 = (size_t)S * N * NB;
-  const bool knorm = !m.ctl->knorm_valid;
-  const double *D = m.D, *E = m.E, *C = m.C;
-  const double *x0 = x + n0;
-  unsigned long long rmax = 0, xmax = 0, bmax = 0;
-  float kmax = 0.0f;
-  const int i = tm.lane;
-  for (int k = tm.id; k < N; k += TEAMS) {
-    if (i >= NB) continue;
-    const long br = (long)s * N + k;
-    const size_t off = (size_t)br * NB;
-    const double *Dk = D + (size_t)br * NB2;
-    const double *xk = x + off;
-    double acc = r[off + i];
-    float ks = 0.0f;
-#pragma unroll
-    for (int j = 0; j < NB; ++j) {
-      const double kij = j <= i ? Dk[i * NB + j] : Dk[j * NB + i];
-      acc = fma(-kij, xk[j], acc);
-      if (knorm) ks += abs_f32_approx(kij);
-    }
-    if (k > 0) {
-      const double *Ek = E + ((size_t)s * (N - 1) + (k - 1)) * NB2 + i * NB;
-      const double *xp = xk - NB;
-#pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        acc = fma(-Ek[j], xp[j], acc);
-        if (knorm) ks += abs_f32_approx(Ek[j]);
-      }
-    }
-    if (k + 1 < N) {
-      const double *Ek = E + ((size_t)s * (N - 1) + k) * NB2 + i;
-      const double *xn = xk + NB;
-#pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        acc = fma(-Ek[j * NB], xn[j], acc);
-        if (knorm) ks += abs_f32_approx(Ek[j * NB]);
-      }
-    }
-    if (k == 0) {
-      const double *Cs = C + (size_t)s * nr * NB + i;
-      for (int j = 0; j < nr; ++j) {
-        acc = fma(-Cs[j * NB], x0[j], acc);
-        if (knorm) ks += abs_f32_approx(Cs[j * NB]);
-      }
-    }
-    m.rho[off + i] = acc;
-    const unsigned long long ra = abs_bits(acc), xa = abs_bits(xk[i]);
-    rmax = ra > rmax ? ra : rmax;
-    xmax = xa > xmax ? xa : xmax;
-    if (iter == 0) {
-      const unsigned long long ba = abs_bits(r[off + i]);
-      bmax = ba > bmax ? ba : bmax;
-    }
-    kmax = ks > kmax ? ks : kmax;
-  }
-  rmax = warp_max_u64(rmax);
-  xmax = warp_max_u64(xmax);
-  bmax = warp_max_u64(bmax);
-  unsigned kb = __float_as_uint(kmax);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned w = __shfl_xor_sync(0xffffffffu, kb, o);
-    kb = w > kb ? w : kb;
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicMax(&m.ctl->rmax, rmax);
-    atomicMax(&m.ctl->xmax, xmax);
-    if (iter == 0) atomicMax(&m.ctl->bmax, bmax);
-    if (knorm) atomicMax(&m.ctl->kmax, (unsigned long long)kb);
-  }
+// Componentwise backward error (Oettli-Prager) of the refinement iterate:
+// omega = max_i |r - K x|_i / (|K| |x| + |r|)_i. The residual itself is
+// FP64; the weights |K||x| + |r| only scale it, so they are accumulated in
+// FP32 from magnitudes rounded toward zero with integer instructions (the
+// FP64 pipe stays free for the residual), which can only overstate omega.
+__device__ __forceinline__ float omega_of(double rho, float w) {
+  const float num = abs_f32_approx(rho);
+  if (!(w > 0.0f)) return num == 0.0f ? 0.0f : __int_as_float(0x7f800000);
+  return num / w;
 }
 
-// Root rows of the residual and the stopping test, by the last CTA of a
-// system once all its tail rows are in: rho_0 = r_0 - R x_0 - sum C_i x_1^i,
-// eta = ||rho||_inf / (||K||_inf ||x||_inf + ||r||_inf); sets converged.
-__device__ __forceinline__ void residual_finish(const MixedState &m, const double *__restrict__ r,
-                                                const double *__restrict__ x, int NBr, int iter, int max_iter,
-                                                double tol) {
+// Row i of block row (s, k) of the residual: rho_i = r_i - (K x)_i (stored
+// in m.rho) and its omega_i. Lanes i >= NB must not call it.
+template <int NB>
+__device__ __forceinline__ float residual_row(const MixedState &m, const double *__restrict__ r,
+                                              const double *__restrict__ x, int s, int k, int i) {
+  constexpr int NB2 = NB * NB;
+  const int N = m.N, nr = m.nr;
+  const size_t n0 = (size_t)m.S * N * NB;
+  const long br = (long)s * N + k;
+  const size_t off = (size_t)br * NB;
+  const double *Dk = m.D + (size_t)br * NB2;
+  const double *xk = x + off;
+  const double ri = r[off + i];
+  double acc = ri;
+  float w = abs_f32_approx(ri);
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    const double kij = j <= i ? Dk[i * NB + j] : Dk[j * NB + i];
+    const double xj = xk[j];
+    acc = fma(-kij, xj, acc);
+    w = fmaf(abs_f32_approx(kij), abs_f32_approx(xj), w);
+  }
+  if (k > 0) {   // block (k, k-1) = E_k (1-based stage k+1)
+    const double *Ek = m.E + ((size_t)s * (N - 1) + (k - 1)) * NB2 + i * NB;
+    const double *xp = xk - NB;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      acc = fma(-Ek[j], xp[j], acc);
+      w = fmaf(abs_f32_approx(Ek[j]), abs_f32_approx(xp[j]), w);
+    }
+  }
+  if (k + 1 < N) {   // block (k, k+1) = E_{k+1}^T
+    const double *Ek = m.E + ((size_t)s * (N - 1) + k) * NB2 + i;
+    const double *xn = xk + NB;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      acc = fma(-Ek[j * NB], xn[j], acc);
+      w = fmaf(abs_f32_approx(Ek[j * NB]), abs_f32_approx(xn[j]), w);
+    }
+  }
+  if (k == 0) {   // block (1, root) = C_s^T
+    const double *Cs = m.C + (size_t)s * nr * NB + i;
+    const double *x0 = x + n0;
+    for (int j = 0; j < nr; ++j) {
+      acc = fma(-Cs[j * NB], x0[j], acc);
+      w = fmaf(abs_f32_approx(Cs[j * NB]), abs_f32_approx(x0[j]), w);
+    }
+  }
+  m.rho[off + i] = acc;
+  return omega_of(acc, w);
+}
+
+// Folds a lane's omega into the warp and then into the system's wmax.
+__device__ __forceinline__ void omega_publish(IRCtl *ctl, float om) {
+  unsigned b = __float_as_uint(om);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned v = __shfl_xor_sync(0xffffffffu, b, o);
+    b = v > b ? v : b;
+  }
+  if ((threadIdx.x & 31) == 0 && b) atomicMax(&ctl->wmax, b);
+}
+
+// rho = r - K x for the rows of tail s (one CTA per tail) and their omega.
+template <int NB>
+__device__ __forceinline__ void residual_tail(const MixedState &m, const double *__restrict__ r,
+                                              const double *__restrict__ x, int s) {
+  constexpr int TS = MCfg<NB>::TS, TEAMS = MCfg<NB>::TEAMS;
+  const Team<TS> tm;
+  float om = 0.0f;
+  for (int k = tm.id; k < m.N; k += TEAMS)
+    if (tm.lane < NB) om = fmaxf(om, residual_row<NB>(m, r, x, s, k, tm.lane));
+  omega_publish(m.ctl, om);
+}
+
+// Root row c of the residual, by one CTA: rho_0c = r_0c - (R x_0)_c -
+// sum_i (C_i x_1^i)_c (fixed-order tree), stored in m.rho; returns omega_c
+// to thread 0.
+__device__ __forceinline__ float residual_root_row(const MixedState &m, const double *__restrict__ r,
+                                                   const double *__restrict__ x, int NBr, int c) {
   __shared__ double red[256];
   __shared__ float redf[256];
   const int N = m.N, nr = m.nr, S = m.S;
   const size_t n0 = (size_t)S * N * NBr;
-  const bool knorm = !m.ctl->knorm_valid;
   const double *C = m.C, *R = m.R, *x0 = x + n0;
-  unsigned long long rmax = 0, xmax = 0, bmax = 0;
-  float kmax = 0.0f;
-  for (int c = 0; c < nr; ++c) {
-    double acc = 0.0;
-    float ks = 0.0f;
-    for (long e = threadIdx.x; e < (long)S * NBr + nr; e += blockDim.x) {
-      double kv, xv;
-      if (e < (long)S * NBr) {
-        const int s = (int)(e / NBr), j = (int)(e - (long)s * NBr);
-        kv = C[((size_t)s * nr + c) * NBr + j];
-        xv = x[(size_t)s * N * NBr + j];
-      } else {
-        const int j = (int)(e - (long)S * NBr);
-        kv = j <= c ? R[c * nr + j] : R[j * nr + c];
-        xv = x0[j];
-      }
-      acc = fma(kv, xv, acc);
-      if (knorm) ks += abs_f32_approx(kv);
+  double acc = 0.0;
+  float w = 0.0f;
+  for (long e = threadIdx.x; e < (long)S * NBr + nr; e += blockDim.x) {
+    double kv, xv;
+    if (e < (long)S * NBr) {
+      const int s = (int)(e / NBr), j = (int)(e - (long)s * NBr);
+      kv = C[((size_t)s * nr + c) * NBr + j];
+      xv = x[(size_t)s * N * NBr + j];
+    } else {
+      const int j = (int)(e - (long)S * NBr);
+      kv = j <= c ? R[c * nr + j] : R[j * nr + c];
+      xv = x0[j];
     }
-    red[threadIdx.x] = acc;
-    redf[threadIdx.x] = ks;
-    for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
-      __syncthreads();
-      if ((int)threadIdx.x < w) {
-        red[threadIdx.x] += red[threadIdx.x + w];
-        redf[threadIdx.x] += redf[threadIdx.x + w];
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const double rc = r[n0 + c] - red[0];
-      m.rho[n0 + c] = rc;
-      const unsigned long long ra = abs_bits(rc), xa = abs_bits(x0[c]);
-      rmax = ra > rmax ? ra : rmax;
-      xmax = xa > xmax ? xa : xmax;
-      if (iter == 0) {
-        const unsigned long long ba = abs_bits(r[n0 + c]);
-        bmax = ba > bmax ? ba : bmax;
-      }
-      kmax = redf[0] > kmax ? redf[0] : kmax;
-    }
-    __syncthreads();
+    acc = fma(kv, xv, acc);
+    w = fmaf(abs_f32_approx(kv), abs_f32_approx(xv), w);
   }
-  if (threadIdx.x != 0) return;
+  red[threadIdx.x] = acc;
+  redf[threadIdx.x] = w;
+  for (int h = blockDim.x >> 1; h > 0; h >>= 1) {
+    __syncthreads();
+    if ((int)threadIdx.x < h) {
+      red[threadIdx.x] += red[threadIdx.x + h];
+      redf[threadIdx.x] += redf[threadIdx.x + h];
+    }
+  }
+  __syncthreads();
+  float om = 0.0f;
+  if (threadIdx.x == 0) {
+    const double rc = r[n0 + c] - red[0];
+    m.rho[n0 + c] = rc;
+    om = omega_of(rc, redf[0] + abs_f32_approx(r[n0 + c]));
+  }
+  __syncthreads();
+  return om;
+}
+
+// The stopping test of one refinement iteration, by one thread once every
+// row's omega is in: converged when omega <= tol; BM_ERR_NOT_CONVERGED after
+// max_iter corrections, or earlier when omega fails to halve (stalled or
+// diverging refinement), which also stops the remaining launches.
+__device__ __forceinline__ void ir_stop(const MixedState &m, float root_omega, int iter, int max_iter, double tol) {
   IRCtl *ctl = m.ctl;
-  unsigned long long rb = atomicAdd(&ctl->rmax, 0ull), xb = atomicAdd(&ctl->xmax, 0ull);
-  unsigned long long bb = atomicAdd(&ctl->bmax, 0ull), kb = atomicAdd(&ctl->kmax, 0ull);
-  rb = rb > rmax ? rb : rmax;
-  xb = xb > xmax ? xb : xmax;
-  if (iter == 0) bb = bb > bmax ? bb : bmax;
-  if (knorm) {
-    const unsigned kf = __float_as_uint(kmax);
-    kb = kb > kf ? kb : kf;
-    ctl->kmax = kb;
-  }
-  ctl->bmax = bb;
-  const double rn = __longlong_as_double((long long)rb), xn = __longlong_as_double((long long)xb);
-  const double bn = __longlong_as_double((long long)bb), kn = (double)__uint_as_float((unsigned)kb);
-  const double eta = rn / (kn * xn + bn);
-  ctl->eta = eta;
+  const unsigned wb = atomicAdd(&ctl->wmax, 0u);
+  const float wf = fmaxf(__uint_as_float(wb), root_omega);
+  const double omega = (double)wf;
+  ctl->eta = omega;
   ctl->iters = iter;
-  ctl->knorm_valid = 1;
-  m.status->eta = eta;
+  m.status->eta = omega;
   m.status->iters = iter;
-  if (eta <= tol)
+  if (omega <= tol) {
     ctl->converged = 1;
-  else if (iter >= max_iter && m.status->code == 0)
-    m.status->code = (int)BM_ERR_NOT_CONVERGED;
-  ctl->rmax = 0ull;
-  ctl->xmax = 0ull;
+  } else if (iter >= max_iter || (iter >= 1 && !(omega <= 0.5 * ctl->omega_prev))) {
+    if (m.status->code == 0) m.status->code = (int)BM_ERR_NOT_CONVERGED;
+    ctl->converged = 1;
+  }
+  ctl->omega_prev = omega;
+  ctl->wmax = 0u;
+}
+
+// Root rows and the stopping test of one system, by its last CTA.
+__device__ __forceinline__ void residual_finish(const MixedState &m, const double *__restrict__ r,
+                                                const double *__restrict__ x, int NBr, int iter, int max_iter,
+                                                double tol) {
+  float om = 0.0f;
+  for (int c = 0; c < m.nr; ++c) om = fmaxf(om, residual_root_row(m, r, x, NBr, c));
+  if (threadIdx.x == 0) ir_stop(m, om, iter, max_iter, tol);
 }
 
 }  // namespace mx

@@ -1,7 +1,8 @@
 """The batched form (bm_batch_*): many systems of uneven S, N, nb, nr
 factored in one persistent launch and solved with FP32 tails + FP64
-refinement. Each system must reach the tolerance against the oracle's FP64
-residual, and must give bitwise the same x as the single-system path
+refinement. Each system must reach the tolerance on the componentwise
+backward error against the oracle's FP64 residual, and must give bitwise the
+same x as the single-system path
 (bm_factor/bm_solve in BM_PREC_FP32_IR) -- the same result alone and in the
 mix. A failing system reports its own status without disturbing the others.
 """
@@ -62,7 +63,7 @@ def test_batch_matches_oracle_and_single_path(tmp_path, monkeypatch):
     for (S, N, nb, nr), d, x, info in zip(shapes, systems, xs, infos):
         assert info["status"] == 0, (S, N, nb, nr, info)
         res = natural.residual(d["D"], d["E"], d["C"], d["R"], x, d["r"])
-        assert res["eta"] <= 1e-12, ((S, N, nb, nr), res["eta"])
+        assert res["omega"] <= 2e-12 and res["eta"] <= 1e-12, ((S, N, nb, nr), res)
         # the same system alone through the single-system path
         g = {k: v.cuda() for k, v in d.items() if isinstance(v, torch.Tensor)}
         single = bm.BranchKKTSolver(S, N, nb, nr, precision=bm.BM_PREC_FP32_IR, tol=1e-12)
@@ -99,7 +100,7 @@ def test_batch_isolates_a_failing_system(tmp_path, monkeypatch):
         assert infos[k]["status"] == 0
         d = systems[k]
         res = natural.residual(d["D"], d["E"], d["C"], d["R"], xs[k], d["r"])
-        assert res["eta"] <= 1e-12
+        assert res["omega"] <= 2e-12
 
 
 def test_batch_rejects_unsupported_shapes():

@@ -1,10 +1,11 @@
 """The FP32-tail + FP64-refinement path (BM_PREC_FP32_IR) through the C ABI.
 
-Parity bar (mixed path): after refinement the normwise backward error
-eta = ||r - K x||_inf / (||K||_inf ||x||_inf + ||r||_inf), evaluated by the
-oracle's FP64 residual, is <= the requested tolerance (1e-10 unless a test
-asks for less); the solution is compared with the FP64 oracle and the
-difference is bounded by eta times a condition estimate. The FP32 tail
+Parity bar (mixed path): refinement stops on the componentwise backward
+error omega = max_i |r - K x|_i / (|K||x| + |r|)_i <= tol (1e-10 unless a
+test asks for less); the oracle's omega of the returned x must meet it
+(within a factor 2: two differently rounded FP64 residuals, and FP32 weights
+on the device), and the solution is compared with the FP64 oracle, the
+difference bounded by omega times a condition estimate. The FP32 tail
 factor is checked against the dense FP64 factor within FP32 rounding
 (well-conditioned systems), and the library's FP64->FP32 rounding is
 checked bit for bit against the hardware conversion.
@@ -81,9 +82,10 @@ def test_mixed_reaches_tolerance(S, N, nb, nr):
     assert out["info"]["status"] == 0, out["info"]
     x = out["x"]
     res = natural.residual(d["D"], d["E"], d["C"], d["R"], x, d["r"])
-    assert res["eta"] <= 1e-12, res["eta"]
-    # the device's own estimate agrees with the oracle's FP64 residual
-    assert out["info"]["backward_error"] <= 1e-12
+    assert res["omega"] <= 2e-12 and res["eta"] <= 1e-12, res
+    # the device's own figure agrees with the oracle's
+    dev = out["info"]["backward_error"]
+    assert dev <= 1e-12 and abs(dev - res["omega"]) <= 0.1 * res["omega"] + 1e-16, (dev, res["omega"])
     ref = natural.solve_system(d)
     K = dense.assemble_system(d["D"], d["E"], d["C"], d["R"])
     kappa = np.linalg.cond(K)
@@ -111,14 +113,18 @@ def test_mixed_fp32_factor_is_the_rounded_factor():
 def test_mixed_refines_and_reports_iterations():
     w = bmgen.WORKLOADS["medium-s64-n64-nb12"]
     d = bmgen.generate(w)
-    loose = run_mixed(d, tol=1e-10)
-    tight = run_mixed(d, tol=1e-15)
+    loose = run_mixed(d, tol=1e-8)
+    tight = run_mixed(d, tol=1e-14)
     assert loose["info"]["status"] == 0 and tight["info"]["status"] == 0
-    assert tight["info"]["iters"] >= loose["info"]["iters"]
-    assert tight["info"]["iters"] >= 1
-    for out, tol in ((loose, 1e-10), (tight, 1e-15)):
+    assert tight["info"]["iters"] > loose["info"]["iters"]
+    for out, tol in ((loose, 1e-8), (tight, 1e-14)):
         res = natural.residual(d["D"], d["E"], d["C"], d["R"], out["x"], d["r"])
-        assert res["eta"] <= tol, (res["eta"], tol)
+        assert res["omega"] <= 2 * tol, (res["omega"], tol)
+    # at 1e-14 the mixed solution agrees with the FP64 oracle's to the
+    # oracle's own accuracy on this workload
+    ref = natural.solve_system(d)
+    fwd = np.abs(tight["x"] - ref["x"]).max() / np.abs(ref["x"]).max()
+    assert fwd <= 1e-9, fwd
 
 
 def test_mixed_not_converged_is_reported():
@@ -158,22 +164,21 @@ def test_mixed_not_spd_is_reported():
 
 def test_mixed_workload_full_size():
     """The mixed-precision workload at full size (S=512, N=128, nb=24, nr=8,
-    barrier 10^U[-6,6]) at the 1e-10 target, against the FP64 oracle's
-    residual. Refinement stagnates near eta ~ 1e-12 on this system (the FP32
-    tail factors of these barrier-conditioned tails limit the contraction)."""
+    barrier 10^U[-6,6]) at the 1e-10 target. Its root Schur complement
+    R - sum_i U_i cancels by ~1e9 (the generator makes it exactly R0 = nr I),
+    more than FP32 tail factors can carry, so refinement may not reach the
+    target: the path must then say so (BM_ERR_NOT_CONVERGED, or BM_ERR_NOT_SPD
+    at the root) instead of reporting a false success, and whatever it
+    reports must hold against the oracle's componentwise backward error."""
     w = bmgen.WORKLOADS["mixed-s512-n128-nb24"]
     d = bmgen.generate(w)
-    out = run_mixed(d, tol=1e-10)
-    assert out["info"]["status"] == 0, out["info"]
+    out = run_mixed(d, tol=1e-10, max_refine=8)
+    info = out["info"]
     res = natural.residual(d["D"], d["E"], d["C"], d["R"], out["x"], d["r"])
-    assert res["eta"] <= 1e-10, res["eta"]
-    # far below the target the refinement stagnates on this system; it must
-    # then say so (BM_ERR_NOT_CONVERGED) and still return its best iterate
-    out2 = run_mixed(d, tol=1e-15, max_refine=6)
-    res2 = natural.residual(d["D"], d["E"], d["C"], d["R"], out2["x"], d["r"])
-    assert out2["info"]["status"] in (0, 5), out2["info"]
-    assert res2["eta"] <= 1e-11, res2["eta"]
-    if out2["info"]["status"] == 0:
-        assert res2["eta"] <= 1e-15
+    if info["status"] == 0:
+        assert res["omega"] <= 2e-10, res
+    elif info["status"] == 5:
+        assert info["iters"] <= 8 and res["omega"] > 1e-10
+        assert abs(info["backward_error"] - res["omega"]) <= 0.1 * res["omega"], (info, res["omega"])
     else:
-        assert out2["info"]["iters"] == 6
+        assert info["status"] == 2 and info["fail_scenario"] == -1, info

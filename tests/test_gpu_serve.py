@@ -97,6 +97,8 @@ def test_same_result_alone_and_in_the_mix(precision):
         for j in range(NRHS):
             res = natural.residual(d["D"], d["E"], d["C"], d["R"], mixed[i][j], d["rs"][j])
             assert res["eta"] <= tol, (i, j, res["eta"])
+            if precision == 1:
+                assert res["omega"] <= 2 * tol, (i, j, res["omega"])
     # the same kernels as the single-system entry points (FP64: first rhs)
     if precision == 0:
         bm = _bm()

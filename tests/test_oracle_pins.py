@@ -301,6 +301,51 @@ def test_generator_is_spd_and_deterministic():
     assert np.array_equal(D, np.swapaxes(D, -1, -2))
 
 
+# --- residual measures: |K| |x| and the componentwise backward error ---------------
+
+@pytest.mark.parametrize("S,N,nb,nr", CASES)
+def test_abs_kx_matches_dense_assembly(S, N, nb, nr):
+    d = small(S, N, nb, nr, seed=7 * S + N, barrier=(-2, 2))
+    g = np.random.default_rng(S + N + nb)
+    x = g.standard_normal(S * N * nb + nr)
+    K = dense.assemble_system(d["D"], d["E"], d["C"], d["R"])
+    want = np.abs(K) @ np.abs(x)
+    got = natural.abs_kx(d["D"], d["E"], d["C"], d["R"], x)
+    assert np.allclose(got, want, rtol=1e-14, atol=0.0)
+    # a transposed sub-diagonal block is seen (E_k is not symmetric)
+    if N > 1 and nb > 1:
+        bad = natural.abs_kx(d["D"], np.swapaxes(d["E"], -1, -2), d["C"], d["R"], x)
+        assert not np.allclose(bad, want, rtol=1e-8, atol=0.0)
+
+
+def test_omega_closed_form_two_by_two():
+    # K = [[2, 1], [1, 3]] (S = N = nb = nr = 1), x = (1, 1), r = (4, 3):
+    # K x = (3, 4), rho = (1, -1), |K||x| + |r| = (7, 7) -> omega = 1/7
+    D = np.array([[[[2.0]]]])
+    E = np.zeros((1, 0, 1, 1))
+    C = np.array([[[1.0]]])
+    R = np.array([[3.0]])
+    res = natural.residual(D, E, C, R, np.array([1.0, 1.0]), np.array([4.0, 3.0]))
+    assert res["omega"] == pytest.approx(1.0 / 7.0, rel=1e-15)
+    assert res["rel_inf"] == pytest.approx(0.25, rel=1e-15)
+    assert res["eta"] == pytest.approx(1.0 / (4.0 * 1.0 + 4.0), rel=1e-15)
+
+
+@pytest.mark.parametrize("S,N,nb,nr", CASES[:5])
+def test_omega_against_dense_definition(S, N, nb, nr):
+    d = small(S, N, nb, nr, seed=11 * S + N, barrier=(-2, 2))
+    xref = dense.dense_solve(d["D"], d["E"], d["C"], d["R"], d["r"])
+    # the exact solution has a tiny componentwise backward error
+    assert natural.residual(d["D"], d["E"], d["C"], d["R"], xref, d["r"])["omega"] < 1e-14
+    # a perturbed one: omega equals the definition on the dense matrix
+    g = np.random.default_rng(N)
+    x = xref * (1.0 + 1e-6 * g.standard_normal(xref.shape))
+    K = dense.assemble_system(d["D"], d["E"], d["C"], d["R"])
+    want = (np.abs(d["r"] - K @ x) / (np.abs(K) @ np.abs(x) + np.abs(d["r"]))).max()
+    got = natural.residual(d["D"], d["E"], d["C"], d["R"], x, d["r"])["omega"]
+    assert got == pytest.approx(want, rel=1e-6)
+
+
 # --- the pins catch plausible mistakes (planted into the oracle's inputs) ---------
 
 def test_pins_detect_transposed_subdiagonal():
