@@ -409,25 +409,41 @@ namespace rows {
 template <int NB>
 struct WCfg {
   static constexpr int TS = 64;
-  static constexpr int LD = NB + 1;
+  // row stride of staged blocks: a multiple of 4 floats, so that rows are
+  // read with 16-byte loads, and 52 mod 32 = 20, so that the eight lanes of
+  // one 16-byte wavefront hit distinct bank groups when they read their own rows
+  static constexpr int LD = (NB + 3) / 4 * 4 + 4;
   static constexpr int SM = NB * LD;
-  // per-team shared memory (elements of T): staged block, factor, two column
-  // buffers, two pivot slots
-  static constexpr int ELEMS = 2 * SM + 2 * NB + 2;
+  // per-team shared memory (elements of T): staged block, factor (stored
+  // by columns), two column buffers, two pivot slots and padding to 16 bytes
+  static constexpr int ELEMS = 2 * SM + 2 * NB + 4;
+  static_assert(NB % 4 == 0, "the wide variant reads blocks as groups of four");
 };
 
 __device__ __forceinline__ void team_bar(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
 
+// Four consecutive floats of shared memory (16-byte aligned).
+__device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ float f4at(const float4 &v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
+
+// Copy an NB x NB float block (global, contiguous) into shared memory with
+// row stride LD, four floats per access.
 template <typename T, int NB>
 __device__ __forceinline__ void stage_w(T *__restrict__ s, const T *__restrict__ g, int lane) {
+  static_assert(sizeof(T) == 4, "wide variant is FP32");
+  constexpr int LD = WCfg<NB>::LD, Q = NB * NB / 4;
+  const float4 *g4 = reinterpret_cast<const float4 *>(g);
 #pragma unroll
-  for (int e = lane; e < NB * NB; e += 64) {
-    const int r = e / NB, c = e - r * NB;
-    s[r * WCfg<NB>::LD + c] = g[e];
+  for (int e = lane; e < Q; e += 64) {
+    const int r = (4 * e) / NB, c = 4 * e - r * NB;
+    *reinterpret_cast<float4 *>(s + r * LD + c) = g4[e];
   }
 }
 
-// Right-looking Cholesky on lane-owned rows with shared-memory exchange.
+// Right-looking Cholesky on lane-owned rows with shared-memory exchange:
+// lane j publishes the pivot, every lane scales its entry of column j and
+// publishes it, then every lane updates its row from the column (read four
+// entries at a time).
 template <typename T, int NB>
 __device__ __forceinline__ int chol_rows_w(T (&d)[NB], T &rinv, int i, T *sCol, T *sPiv, int bar) {
   int fail = 0;
@@ -451,36 +467,88 @@ __device__ __forceinline__ int chol_rows_w(T (&d)[NB], T &rinv, int i, T *sCol, 
     if (i < NB) col[i] = d[j];
     team_bar(bar);
 #pragma unroll
-    for (int k = j + 1; k < NB; ++k) d[k] = fma_t<T>(-d[j], col[k], d[k]);
+    for (int g = (j + 1) / 4; g < NB / 4; ++g) {
+      const float4 v = lds4(col + 4 * g);
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (4 * g + e > j) d[4 * g + e] = fma_t<T>(-d[j], f4at(v, e), d[4 * g + e]);
+    }
   }
   return fail;
 }
 
-// x := x L^{-T} for a lane-owned row, L staged in sL (row stride LD), sInv.
+// x := x L^{-T} for a lane-owned row; the factor is staged by columns
+// (sLt[j * LD + k] = L_kj), sInv holds 1 / L_jj.
 template <typename T, int NB>
-__device__ __forceinline__ void trsm_row_w(T (&x)[NB], const T *sL, const T *sInv) {
+__device__ __forceinline__ void trsm_row_w(T (&x)[NB], const T *sLt, const T *sInv) {
   constexpr int LD = WCfg<NB>::LD;
 #pragma unroll
   for (int j = 0; j < NB; ++j) {
     x[j] *= sInv[j];
 #pragma unroll
-    for (int k = j + 1; k < NB; ++k) x[k] = fma_t<T>(-x[j], sL[k * LD + j], x[k]);
+    for (int g = (j + 1) / 4; g < NB / 4; ++g) {
+      const float4 v = lds4(sLt + j * LD + 4 * g);
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (4 * g + e > j) x[4 * g + e] = fma_t<T>(-x[j], f4at(v, e), x[4 * g + e]);
+    }
   }
 }
 
+// acc_j = sum_k a[k] X[j][k] for every row j of the staged block, each row
+// read four entries at a time; out[j] = sign * acc_j (+ out[j] if ADD).
+template <typename T, int NB, bool ADD>
+__device__ __forceinline__ void rowdot_w(T (&out)[NB], const T (&a)[NB], const T *__restrict__ sX, T sign) {
+  constexpr int LD = WCfg<NB>::LD;
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    T acc = T(0);
+#pragma unroll
+    for (int g = 0; g < NB / 4; ++g) {
+      const float4 v = lds4(sX + j * LD + 4 * g);
+      acc = fma_t<T>(a[4 * g + 0], v.x, acc);
+      acc = fma_t<T>(a[4 * g + 1], v.y, acc);
+      acc = fma_t<T>(a[4 * g + 2], v.z, acc);
+      acc = fma_t<T>(a[4 * g + 3], v.w, acc);
+    }
+    out[j] = ADD ? out[j] + sign * acc : sign * acc;
+  }
+}
+
+// d[j] -= sum_k X[i][k] X[j][k] for all j, X staged in sX, row i = lane.
 template <typename T, int NB>
 __device__ __forceinline__ void syrk_row_w(T (&d)[NB], const T *__restrict__ sX, int ir) {
   constexpr int LD = WCfg<NB>::LD;
   T xi[NB];
 #pragma unroll
-  for (int k = 0; k < NB; ++k) xi[k] = sX[ir * LD + k];
-#pragma unroll
-  for (int j = 0; j < NB; ++j) {
-    T acc = T(0);
-#pragma unroll
-    for (int k = 0; k < NB; ++k) acc = fma_t<T>(xi[k], sX[j * LD + k], acc);
-    d[j] -= acc;
+  for (int g = 0; g < NB / 4; ++g) {
+    const float4 v = lds4(sX + ir * LD + 4 * g);
+    xi[4 * g] = v.x;
+    xi[4 * g + 1] = v.y;
+    xi[4 * g + 2] = v.z;
+    xi[4 * g + 3] = v.w;
   }
+  rowdot_w<T, NB, true>(d, xi, sX, T(-1));
+}
+
+// Row ir of a float block row (16-byte aligned) into registers.
+template <typename T, int NB>
+__device__ __forceinline__ void load_row4(T (&d)[NB], const T *__restrict__ row) {
+  const float4 *r4 = reinterpret_cast<const float4 *>(row);
+#pragma unroll
+  for (int g = 0; g < NB / 4; ++g) {
+    const float4 v = r4[g];
+    d[4 * g] = v.x;
+    d[4 * g + 1] = v.y;
+    d[4 * g + 2] = v.z;
+    d[4 * g + 3] = v.w;
+  }
+}
+template <typename T, int NB>
+__device__ __forceinline__ void store_row4(T *__restrict__ row, const T (&d)[NB]) {
+  float4 *r4 = reinterpret_cast<float4 *>(row);
+#pragma unroll
+  for (int g = 0; g < NB / 4; ++g) r4[g] = make_float4(d[4 * g], d[4 * g + 1], d[4 * g + 2], d[4 * g + 3]);
 }
 
 // One task of level lvl, wide team (sbuf: WCfg<NB>::ELEMS elements of T).
@@ -500,9 +568,7 @@ __device__ __forceinline__ void factor_task_rows_w(const TailView<T> &v, T *sbuf
 #pragma unroll
     for (int j = 0; j < NB; ++j) d[j] = to_t<T>(j <= ir ? Dq[ir * NB + j] : Dq[j * NB + ir]);
   } else {
-    const T *Dq = v.Dt + (sb + (N - q)) * NB2 + ir * NB;
-#pragma unroll
-    for (int j = 0; j < NB; ++j) d[j] = Dq[j];
+    load_row4<T, NB>(d, v.Dt + (sb + (N - q)) * NB2 + ir * NB);
   }
   if (lvl >= 1) {
     const int h = 1 << (lvl - 1);
@@ -528,11 +594,7 @@ __device__ __forceinline__ void factor_task_rows_w(const TailView<T> &v, T *sbuf
     }
   }
   if (!elim) {
-    if (act) {
-      T *o = v.Dt + (sb + (N - q)) * NB2 + i * NB;
-#pragma unroll
-      for (int j = 0; j < NB; ++j) o[j] = d[j];
-    }
+    if (act) store_row4<T, NB>(v.Dt + (sb + (N - q)) * NB2 + i * NB, d);
     return;
   }
   const int hh = 1 << lvl;
@@ -542,13 +604,12 @@ __device__ __forceinline__ void factor_task_rows_w(const TailView<T> &v, T *sbuf
   const int fail = chol_rows_w<T, NB>(d, rinv, i, sCol, sPiv, bar);
   if (i == 0 && fail) report_not_spd(v.status, s, N + 1 - q);
   if (act) {
-    T *Ld = v.Ld + (sb + (N - q)) * NB2 + i * NB;
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
-      const T l = j <= i ? d[j] : T(0);
-      Ld[j] = l;
-      sL[i * LD + j] = l;
+      if (j > i) d[j] = T(0);
+      sL[j * LD + i] = d[j];   // by columns: sL[j][k] = L_kj
     }
+    store_row4<T, NB>(v.Ld + (sb + (N - q)) * NB2 + i * NB, d);
     sCol[i] = rinv;   // inverse diagonal (column buffers are free now)
     v.invd[(sb + (N - q)) * NB + i] = rinv;
   }
@@ -567,17 +628,15 @@ __device__ __forceinline__ void factor_task_rows_w(const TailView<T> &v, T *sbuf
     }
     trsm_row_w<T, NB>(av, sL, sCol);
     if (act) {
-      T *La = v.Ll + (sb + (N - q)) * NB2 + i * NB;
+      store_row4<T, NB>(v.Ll + (sb + (N - q)) * NB2 + i * NB, av);
+      float4 *x4 = reinterpret_cast<float4 *>(sX + i * LD);
 #pragma unroll
-      for (int k = 0; k < NB; ++k) {
-        La[k] = av[k];
-        sX[i * LD + k] = av[k];
-      }
+      for (int g = 0; g < NB / 4; ++g) x4[g] = make_float4(av[4 * g], av[4 * g + 1], av[4 * g + 2], av[4 * g + 3]);
     }
   } else if (act) {
-    T *La = v.Ll + (sb + (N - q)) * NB2 + i * NB;
+    float4 *La = reinterpret_cast<float4 *>(v.Ll + (sb + (N - q)) * NB2 + i * NB);
 #pragma unroll
-    for (int k = 0; k < NB; ++k) La[k] = T(0);
+    for (int g = 0; g < NB / 4; ++g) La[g] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   // right coupling: L_{b,q} = M_{b,q} L^{-T}
   T b[NB];
@@ -586,27 +645,17 @@ __device__ __forceinline__ void factor_task_rows_w(const TailView<T> &v, T *sbuf
 #pragma unroll
     for (int k = 0; k < NB; ++k) b[k] = to_t<T>(Eb[k * NB + ir]);
   } else {
-    const T *Wb = v.W + (sb + (N - q)) * NB2 + ir * NB;
-#pragma unroll
-    for (int k = 0; k < NB; ++k) b[k] = Wb[k];
+    load_row4<T, NB>(b, v.W + (sb + (N - q)) * NB2 + ir * NB);
   }
   trsm_row_w<T, NB>(b, sL, sCol);
-  if (act) {
-    T *Lb = v.Lr + (sb + (N - q)) * NB2 + i * NB;
-#pragma unroll
-    for (int k = 0; k < NB; ++k) Lb[k] = b[k];
-  }
+  if (act) store_row4<T, NB>(v.Lr + (sb + (N - q)) * NB2 + i * NB, b);
   if (hasA) {
+    // fill M_{b,a} = -L_{b,q} L_{a,q}^T (rows of L_{a,q} staged in sX)
     team_bar(bar);
     if (act) {
-      T *Wo = v.W + (sb + (N - a)) * NB2 + i * NB;
-#pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        T acc = T(0);
-#pragma unroll
-        for (int k = 0; k < NB; ++k) acc = fma_t<T>(b[k], sX[j * LD + k], acc);
-        Wo[j] = -acc;
-      }
+      T w[NB];
+      rowdot_w<T, NB, false>(w, b, sX, T(-1));
+      store_row4<T, NB>(v.W + (sb + (N - a)) * NB2 + i * NB, w);
     }
   }
   team_bar(bar);
@@ -634,9 +683,7 @@ __device__ __forceinline__ void x1_task_rows_w(const TailView<T> &v, void *sbuf,
 #pragma unroll
     for (int j = 0; j < NB; ++j) d[j] = to_t<T>(j <= ir ? Dq[ir * NB + j] : Dq[j * NB + ir]);
   } else {
-    const T *Dq = v.Dt + sb * NB2 + ir * NB;
-#pragma unroll
-    for (int j = 0; j < NB; ++j) d[j] = Dq[j];
+    load_row4<T, NB>(d, v.Dt + sb * NB2 + ir * NB);
   }
   if (Lc >= 1) {
     const int m = 1 << (Lc - 1);
@@ -649,20 +696,23 @@ __device__ __forceinline__ void x1_task_rows_w(const TailView<T> &v, void *sbuf,
   const int fail = chol_rows_w<T, NB>(d, rinv, i, sCol, sPiv, bar);
   if (i == 0 && fail) report_not_spd(v.status, s, 1);
   if (act) {
+    T z[NB];
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
-      const T l = j <= i ? d[j] : T(0);
-      v.Ld[sb * NB2 + i * NB + j] = l;
-      sL[i * LD + j] = l;
-      v.Lr[sb * NB2 + i * NB + j] = T(0);
-      v.Ll[sb * NB2 + i * NB + j] = T(0);
+      if (j > i) d[j] = T(0);
+      sL[j * LD + i] = d[j];   // by columns: sL[j][k] = L_kj
+      z[j] = T(0);
     }
+    store_row4<T, NB>(v.Ld + sb * NB2 + i * NB, d);
+    store_row4<T, NB>(v.Lr + sb * NB2 + i * NB, z);
+    store_row4<T, NB>(v.Ll + sb * NB2 + i * NB, z);
     v.invd[sb * NB + i] = rinv;
   }
   team_bar(bar);
   if (act) sCol[i] = rinv;
   for (int e = lane; e < nr * NB; e += 64) sC[e] = v.C[(size_t)s * nr * NB + e];
   team_bar(bar);
+  // F = C L^{-T} in FP64, one row of C per lane (column sweep within the row)
   for (int c = lane; c < nr; c += 64) {
     double f[NB];
 #pragma unroll
@@ -671,7 +721,7 @@ __device__ __forceinline__ void x1_task_rows_w(const TailView<T> &v, void *sbuf,
     for (int j = 0; j < NB; ++j) {
       f[j] *= to_d<T>(sCol[j]);
 #pragma unroll
-      for (int k = j + 1; k < NB; ++k) f[k] = fma(-f[j], to_d<T>(sL[k * LD + j]), f[k]);
+      for (int k = j + 1; k < NB; ++k) f[k] = fma(-f[j], to_d<T>(sL[j * LD + k]), f[k]);
     }
 #pragma unroll
     for (int k = 0; k < NB; ++k) {
