@@ -73,6 +73,69 @@ __device__ __forceinline__ bool ir_done(const IRCtl *ctl) {
   return *((volatile const int *)&ctl->converged) != 0;
 }
 
+// z - sum_k L[k] y[k] over one row of a tail block (row-major, contiguous)
+// and a vector written by other CTAs (read through L2), k in increasing
+// order; four entries per load when the rows are 16-byte aligned.
+template <int NB>
+__device__ __forceinline__ float row_dot_sub(const float *__restrict__ L, const float *y, float z) {
+  if constexpr (NB % 4 == 0) {
+    const float4 *L4 = reinterpret_cast<const float4 *>(L);
+    const float4 *y4 = reinterpret_cast<const float4 *>(y);
+#pragma unroll
+    for (int g = 0; g < NB / 4; ++g) {
+      const float4 l = L4[g], v = __ldcg(y4 + g);
+      z = fmaf(-l.x, v.x, z);
+      z = fmaf(-l.y, v.y, z);
+      z = fmaf(-l.z, v.z, z);
+      z = fmaf(-l.w, v.w, z);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < NB; ++k) z = fmaf(-L[k], __ldcg(y + k), z);
+  }
+  return z;
+}
+
+// The same with the column of a block (L[k * NB], coalesced over the team)
+// and the vector read four entries per load.
+template <int NB>
+__device__ __forceinline__ float col_dot_sub(const float *__restrict__ L, const float *y, float z) {
+  if constexpr (NB % 4 == 0) {
+    const float4 *y4 = reinterpret_cast<const float4 *>(y);
+#pragma unroll
+    for (int g = 0; g < NB / 4; ++g) {
+      const float4 v = __ldcg(y4 + g);
+      z = fmaf(-L[(4 * g) * NB], v.x, z);
+      z = fmaf(-L[(4 * g + 1) * NB], v.y, z);
+      z = fmaf(-L[(4 * g + 2) * NB], v.z, z);
+      z = fmaf(-L[(4 * g + 3) * NB], v.w, z);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < NB; ++k) z = fmaf(-L[k * NB], __ldcg(y + k), z);
+  }
+  return z;
+}
+
+// One contiguous row of a block into registers (four floats per load when aligned).
+template <int NB>
+__device__ __forceinline__ void load_row(float (&r)[NB], const float *__restrict__ p) {
+  if constexpr (NB % 4 == 0) {
+    const float4 *p4 = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+    for (int g = 0; g < NB / 4; ++g) {
+      const float4 v = p4[g];
+      r[4 * g] = v.x;
+      r[4 * g + 1] = v.y;
+      r[4 * g + 2] = v.z;
+      r[4 * g + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < NB; ++k) r[k] = p[k];
+  }
+}
+
 // Forward substitution of one tail in FP32 (all levels, then x_1 and
 // t_i = F_{i,1} y_1 in FP64); the last CTA of the grid does the root step
 // of Alg. 2 in FP64 and stores the root correction d_0 (and x_0 += d_0).
@@ -110,18 +173,8 @@ __device__ __forceinline__ void fwd_tail(const MixedState &m, const double *__re
             const int mm = ((N - 1) >> (lvl - 1)) << (lvl - 1);
             if (ctz32(mm) == lvl - 1) pl = mm;
           }
-          if (pl) {
-            const float *L = m.Lr + (sb + (N - pl)) * NB2 + i * NB;
-            const float *y = m.y + (sb + (N - pl)) * NB;
-#pragma unroll
-            for (int k = 0; k < NB; ++k) z = fmaf(-L[k], __ldcg(y + k), z);
-          }
-          if (pr) {
-            const float *L = m.Ll + (sb + (N - pr)) * NB2 + i * NB;
-            const float *y = m.y + (sb + (N - pr)) * NB;
-#pragma unroll
-            for (int k = 0; k < NB; ++k) z = fmaf(-L[k], __ldcg(y + k), z);
-          }
+          if (pl) z = row_dot_sub<NB>(m.Lr + (sb + (N - pl)) * NB2 + i * NB, m.y + (sb + (N - pl)) * NB, z);
+          if (pr) z = row_dot_sub<NB>(m.Ll + (sb + (N - pr)) * NB2 + i * NB, m.y + (sb + (N - pr)) * NB, z);
         }
       }
       if (!elim) {
@@ -129,9 +182,7 @@ __device__ __forceinline__ void fwd_tail(const MixedState &m, const double *__re
         continue;
       }
       float Lrow[NB];
-      const float *Ld = m.Ld + (sb + (N - q)) * NB2 + (i < NB ? i : 0) * NB;
-#pragma unroll
-      for (int k = 0; k < NB; ++k) Lrow[k] = Ld[k];
+      load_row<NB>(Lrow, m.Ld + (sb + (N - q)) * NB2 + (i < NB ? i : 0) * NB);
       const float inv = i < NB ? m.invd[zoff + i] : 0.0f;
       if (TS <= 32) {
         const int base = (threadIdx.x & 31) & ~(TS - 1);
@@ -253,16 +304,8 @@ __device__ __forceinline__ void bwd_tail(const MixedState &m, double *x, int ite
           z = m.y[zoff + i];
           const int h = 1 << lvl;
           const int a = q - h, b = (q + h <= N - 1) ? q + h : N;
-          const float *Lb = m.Lr + (sb + (N - q)) * NB2 + i;
-          const float *db = m.y + (sb + (N - b)) * NB;
-#pragma unroll
-          for (int k = 0; k < NB; ++k) z = fmaf(-Lb[k * NB], __ldcg(db + k), z);
-          if (q > h) {
-            const float *La = m.Ll + (sb + (N - q)) * NB2 + i;
-            const float *da = m.y + (sb + (N - a)) * NB;
-#pragma unroll
-            for (int k = 0; k < NB; ++k) z = fmaf(-La[k * NB], __ldcg(da + k), z);
-          }
+          z = col_dot_sub<NB>(m.Lr + (sb + (N - q)) * NB2 + i, m.y + (sb + (N - b)) * NB, z);
+          if (q > h) z = col_dot_sub<NB>(m.Ll + (sb + (N - q)) * NB2 + i, m.y + (sb + (N - a)) * NB, z);
         }
       }
       float Lcol[NB];
