@@ -48,24 +48,23 @@ __global__ void __launch_bounds__(256) k_mixed_bwd(MixedState m, double *x, int 
 }
 
 // rho = r - K x in FP64 and the componentwise backward error of the
-// iterate; one team of NB lanes per (tail, stage) block row (row i of the
-// block per lane), one more CTA-strided pass over the root rows. The last
-// CTA applies the stopping test.
+// iterate; one thread per row of the tails (grid-stride; every lane of an
+// FP64 warp instruction does useful work), one more CTA-strided pass over
+// the root rows. The last CTA applies the stopping test.
 template <int NB>
 __global__ void __launch_bounds__(256) k_mixed_residual(MixedState m, const double *__restrict__ r,
                                                          const double *__restrict__ x, int iter, int max_iter,
                                                          double tol) {
-  constexpr int TS = MCfg<NB>::TS, TEAMS = MCfg<NB>::TEAMS;
   __shared__ unsigned sroot;
-  const Team<TS> tm;
   pdl_wait();
   if (ir_done(m.ctl)) return;
-  const long nrow = (long)m.S * m.N;
+  const long nrow = (long)m.S * m.N * NB;
   float om = 0.0f;
-  for (long br = (long)blockIdx.x * TEAMS + tm.id; br < nrow; br += (long)gridDim.x * TEAMS) {
-    if (tm.lane >= NB) continue;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < nrow; e += (long)gridDim.x * blockDim.x) {
+    const long br = e / NB;
+    const int i = (int)(e - br * NB);
     const int s = (int)(br / m.N), k = (int)(br - (long)s * m.N);
-    om = fmaxf(om, residual_row<NB>(m, r, x, s, k, tm.lane));
+    om = fmaxf(om, residual_row<NB>(m, r, x, s, k, i));
   }
   omega_publish(m.ctl, om);
   // root rows; their omega goes through the same maximum
@@ -119,8 +118,8 @@ void launch_iteration(const MixedState &m, const double *r, double *x, int iter,
   const double *rhs = iter == 0 ? r : m.rho;
   launch_cluster(k_mixed_fwd<NB>, grid, 256, CS, st, m, rhs, x, iter, CS);
   launch_cluster(k_mixed_bwd<NB>, grid, 256, CS, st, m, x, iter, CS);
-  const long rows = (long)m.S * m.N;
-  long blocks = (rows + MCfg<NB>::TEAMS - 1) / MCfg<NB>::TEAMS;
+  const long rows = (long)m.S * m.N * NB;
+  long blocks = (rows + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
   if (blocks < m.nr) blocks = m.nr;
   launch_pdl(k_mixed_residual<NB>, (unsigned)blocks, 256, 0, st, m, r, (const double *)x, iter, max_iter, tol);

@@ -423,14 +423,17 @@ __device__ __forceinline__ void omega_publish(IRCtl *ctl, float om) {
 }
 
 // rho = r - K x for the rows of tail s (one CTA per tail) and their omega.
+// One thread per row of the tail, so that every lane of an FP64 warp
+// instruction does useful work (the FP64 pipe charges whole warps).
 template <int NB>
 __device__ __forceinline__ void residual_tail(const MixedState &m, const double *__restrict__ r,
                                               const double *__restrict__ x, int s) {
-  constexpr int TS = MCfg<NB>::TS, TEAMS = MCfg<NB>::TEAMS;
-  const Team<TS> tm;
   float om = 0.0f;
-  for (int k = tm.id; k < m.N; k += TEAMS)
-    if (tm.lane < NB) om = fmaxf(om, residual_row<NB>(m, r, x, s, k, tm.lane));
+  const int rows = m.N * NB;
+  for (int e = threadIdx.x; e < rows; e += blockDim.x) {
+    const int k = e / NB, i = e - k * NB;
+    om = fmaxf(om, residual_row<NB>(m, r, x, s, k, i));
+  }
   omega_publish(m.ctl, om);
 }
 
