@@ -44,7 +44,7 @@ from typing import Optional, Tuple
 
 import torch
 
-__all__ = ["Workload", "WORKLOADS", "generate", "n_unknowns", "seed_for",
+__all__ = ["Workload", "WORKLOADS", "generate", "generate_qp", "n_unknowns", "seed_for",
            "method_flops", "natural_flops", "draw_batched_shapes"]
 
 
@@ -216,3 +216,36 @@ def draw_batched_shapes(count: int = 256, seed: int = 4000, nb_set=(6, 12, 24, 4
         nb = int(nb_set[int(torch.randint(0, len(nb_set), (1,), generator=g))])
         shapes.append((S, N, nb, -(-nb // 3)))
     return shapes
+
+
+def generate_qp(S: int, N: int, nx: int, nu: int, seed: int = 0, device="cpu",
+                barrier: Tuple[float, float] = (-3.0, 3.0), tau: float = 1e-6, delta: float = 1e-4) -> dict:
+    """Draw the data of a branch-MPC QP (inputs of the assembly front end).
+
+    Stage k = 1..N of scenario s holds z_k = (x_k, u_k) (nb = nx + nu; u_N
+    is the padding input of the last stage); the shared root is the first
+    input u_0 (nr = nu); the initial state is fixed. Dynamics
+    x_{k+1} = A_k x_k + B_k u_k (k = 1..N-1) and x_1 = A_0 x_init + B_0 u_0.
+    Returns float64 tensors A[S][N][nx][nx] (A_k at index k; A_0 only acts on
+    the fixed initial state), B[S][N][nx][nu] (B_k at index k), diagonal
+    costs q[S][N][nx] (x_1..x_N), rw[S][N][nu] (u_1..u_N), r0w[nu] (u_0),
+    inequality weights w[S][N][nb] and w0[nu] (the positive diagonal W of
+    the interior point method, 10^U[lo, hi]) and the regularizations tau,
+    delta. Draws only: no assembly here."""
+    dev = torch.device(device)
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    f64 = torch.float64
+    eye = torch.eye(nx, dtype=f64, device=dev)
+    A0 = eye + 0.1 * torch.randn((nx, nx), generator=g, device=dev, dtype=f64) / (nx ** 0.5)
+    A = A0.expand(S, N, nx, nx) + 0.02 * torch.randn((S, N, nx, nx), generator=g, device=dev, dtype=f64)
+    B = torch.randn((S, N, nx, nu), generator=g, device=dev, dtype=f64) / (nx ** 0.5)
+    q = _uniform(g, (S, N, nx), 0.1, 10.0, dev)
+    rw = _uniform(g, (S, N, nu), 0.1, 10.0, dev)
+    r0w = _uniform(g, (nu,), 0.1, 10.0, dev)
+    lo, hi = barrier
+    w = torch.pow(10.0, _uniform(g, (S, N, nx + nu), lo, hi, dev))
+    w0 = torch.pow(10.0, _uniform(g, (nu,), lo, hi, dev))
+    return {"A": A.contiguous(), "B": B.contiguous(), "q": q, "rw": rw, "r0w": r0w, "w": w, "w0": w0,
+            "tau": float(tau), "delta": float(delta), "S": S, "N": N, "nx": nx, "nu": nu,
+            "nb": nx + nu, "nr": nu}
