@@ -525,6 +525,92 @@ def run_serving(args):
     return 0
 
 
+def run_assembly(args):
+    """Assembly front end: App. A's reduced matrix of a branch-MPC QP formed
+    on the GPU (bm_assemble_reduced) in the solver's block layout, timed
+    alone (value: GB/s of inputs read and D, E, C, R written once; roofline:
+    the FP64 FMAs of the [A_k B_k]^T [A_k B_k] lower triangles, which bound
+    it on GB300), then QP -> K -> factor -> solve with the FP64 path and with
+    FP32+IR."""
+    import torch
+
+    import bmgen
+    import paper_2609_29977_gb300 as bm
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    S, N, nx, nu = (int(t) for t in (args.shape or "512,128,24,8").split(","))
+    qp = bmgen.generate_qp(S, N, nx, nu, seed=6000, device=dev, barrier=(-3.0, 3.0), delta=1e-2)
+    nb = nx + nu
+    for _ in range(max(3, args.warmup)):
+        out = bm.bm_assemble_reduced(qp)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    k = min(args.steps, 200)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+    sampler = ClockSampler("0")
+    sampler.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    for a, b in ev:
+        flush.zero_()
+        a.record(stream)
+        out = bm.bm_assemble_reduced(qp)
+        b.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    n_in = sum(qp[key].numel() for key in ("A", "B", "q", "rw", "r0w", "w", "w0"))
+    n_out = sum(out[key].numel() for key in ("D", "E", "C", "R"))
+    byts = 8.0 * (n_in + n_out)
+    peaks, src = _peaks()
+    gbs = byts / (ms * 1e-3) / 1e9
+    flops = 2.0 * nx * (nb * (nb + 1) / 2) * S * (N - 1) + 2.0 * nx * nu * nu * S
+    gflops = flops / (ms * 1e-3) / 1e9
+    n = bmgen.n_unknowns(S, N, nb, nu)
+    r = torch.randn(n, dtype=torch.float64, device=dev, generator=torch.Generator(device=dev).manual_seed(6001))
+    paths = {}
+    for name, prec in (("fp64", bm.BM_PREC_FP64), ("fp32ir", bm.BM_PREC_FP32_IR)):
+        solver = bm.BranchKKTSolver(S, N, nb, nu, precision=prec, max_refine=args.max_refine, tol=args.tol)
+        x = torch.empty_like(r)
+        for _ in range(3):
+            o2 = bm.bm_assemble_reduced(qp)
+            solver.factor(o2["D"], o2["E"], o2["C"], o2["R"])
+            solver.solve(r, x)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tt = []
+        for _ in range(5):
+            flush.zero_()
+            a.record(stream)
+            o2 = bm.bm_assemble_reduced(qp)
+            solver.factor(o2["D"], o2["E"], o2["C"], o2["R"])
+            solver.solve(r, x)
+            b.record(stream)
+            torch.cuda.synchronize()
+            tt.append(a.elapsed_time(b))
+        info = solver.query()
+        meas = gpu_residual_measures({"D": o2["D"], "E": o2["E"], "C": o2["C"], "R": o2["R"], "r": r}, x)
+        paths[name] = {"ms_qp_to_solution": statistics.median(tt), "device_status": info["name"],
+                       "refinement_steps": info["iters"], **meas}
+        solver.close()
+    line = {
+        "metric": "assembly front end: GB/s of K formed from QP data; QP -> solution ms", "value": gbs,
+        "unit": "GB/s", "n_gpus": 1, "steps": k, "warmup": max(3, args.warmup), "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic branch-MPC QP (seeded)",
+        "config": {"workload": "qp-assembly-s%d-n%d-nx%d-nu%d" % (S, N, nx, nu), "S": S, "N": N, "nx": nx,
+                   "nu": nu, "l2": "flushed between timed steps"},
+        "roofline": {"kernel": "k_assemble_stage + k_assemble_coupling + k_assemble_root", "bound": "alu", "achieved": gflops,
+                     "peak": fp64_peak_gflops(), "unit": "GFLOP/s", "frac": gflops / fp64_peak_gflops(),
+                     "traffic": None, "peak_source": "FP64 ALU derived (as the factor)",
+                     "algorithmic_flops": flops, "algorithmic_bytes": byts,
+                     "hbm_frac": gbs / peaks["hbm_gbs"], "hbm_peak_source": src},
+        "paths": paths, "clocks": clocks, "gpu_launches": 3 * k,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_gpu(args):
     import torch
 
@@ -732,6 +818,8 @@ def main():
         return run_batched(args)
     if args.workload.startswith("serving"):
         return run_serving(args)
+    if args.workload.startswith("assembly"):
+        return run_assembly(args)
     return run_gpu(args)
 
 

@@ -219,6 +219,39 @@ bm_status bm_factor_solve_noalloc(int S, int N, int nb, int nr, const double *D,
 bm_status bm_round_to_fp32(const double *src, float *dst, size_t n, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Assembly front end (App. A, "Linear System Sparsity in IPM and ADMM"):
+ * forms the reduced SPD matrix of a branch-MPC QP,
+ *     K = P + tau I + delta^{-1} A^T A + G^T (W + delta I)^{-1} G,
+ * the matrix left after eliminating the equality and inequality multipliers
+ * from the regularized KKT matrix of an interior point method (Eq.
+ * appendix_ipm_kkt; ADMM's Eq. appendix_admm_kkt has the same form with
+ * tau = sigma, delta = 1/rho and W = 0), directly in the D, E, C, R layout
+ * of bm_factor (nb = nx + nu, nr = nu).
+ *
+ * Stage k = 1..N of a scenario holds z_k = (x_k, u_k) (u_N pads the last
+ * stage); the root is the first input u_0; the initial state is fixed. The
+ * equality rows are x_1 - B_0 u_0 = A_0 x_init and
+ * x_{k+1} - A_k x_k - B_k u_k = 0 (k = 1..N-1); G = I (bounds on every
+ * variable). All arrays are DEVICE, row-major float64:
+ *   A[S][N][nx][nx], B[S][N][nx][nu]  A_k, B_k at index k (A_0 is not read),
+ *   q[S][N][nx], rw[S][N][nu]         diagonal costs of x_k and u_k (index k-1),
+ *   r0w[nu]                           diagonal cost of u_0,
+ *   w[S][N][nx+nu], w0[nu]            the positive diagonal W (one entry per
+ *                                     variable, same order).
+ * Outputs D, E, C, R (full symmetric D and R) are overwritten. Asynchronous
+ * on stream. Errors: BM_ERR_INVALID_ARG (sizes, tau < 0, delta <= 0, NULL),
+ * BM_ERR_CUDA. The paper has no kernel for this step; its formula is App. A's.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int S, N, nx, nu;   /* scenarios, horizon, state and input sizes (nx + nu <= 64) */
+  double tau, delta;  /* regularizations (tau >= 0, delta > 0) */
+} bm_qp_desc;
+
+bm_status bm_assemble_reduced(const bm_qp_desc *d, const double *A, const double *B, const double *q,
+                              const double *rw, const double *r0w, const double *w, const double *w0,
+                              double *D, double *E, double *C, double *R, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Batched form: many independent systems of uneven S, N, nb (and nr) in one
  * object, solved with the mixed-precision method (FP32 tails, FP64 root,
  * FP64 iterative refinement). Not in the paper; every system is the one of

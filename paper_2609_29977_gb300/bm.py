@@ -27,7 +27,8 @@ EXPORTED_SYMBOLS = ("bm_version", "bm_status_string", "bm_workspace_bytes", "bm_
                     "bm_factor_solve_noalloc", "bm_round_to_fp32", "bm_batch_workspace_bytes",
                     "bm_batch_analyze", "bm_batch_factor", "bm_batch_solve", "bm_batch_query",
                     "bm_batch_schedule", "bm_batch_destroy", "bm_server_request_bytes", "bm_server_create",
-                    "bm_server_submit", "bm_server_poll", "bm_server_get_stats", "bm_server_destroy")
+                    "bm_server_submit", "bm_server_poll", "bm_server_get_stats", "bm_server_destroy",
+                    "bm_assemble_reduced")
 BATCH_NB = (4, 6, 12, 24, 48)
 BM_NOALLOC_SCRATCH_BYTES = 32 << 20
 BM_SERVE_MAX_RHS = 8
@@ -45,6 +46,11 @@ class bm_desc(ctypes.Structure):
 class bm_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("fail_scenario", ctypes.c_int), ("fail_stage", ctypes.c_int),
                 ("iters", ctypes.c_int), ("backward_error", ctypes.c_double)]
+
+
+class bm_qp_desc(ctypes.Structure):
+    _fields_ = [("S", ctypes.c_int), ("N", ctypes.c_int), ("nx", ctypes.c_int), ("nu", ctypes.c_int),
+                ("tau", ctypes.c_double), ("delta", ctypes.c_double)]
 
 
 class bm_server_desc(ctypes.Structure):
@@ -135,6 +141,8 @@ def _load():
     lib.bm_round_to_fp32.argtypes = [dp, dp, ctypes.c_size_t, vp]
     lib.bm_factor_solve_noalloc.restype = ctypes.c_int
     lib.bm_factor_solve_noalloc.argtypes = [ctypes.c_int] * 4 + [dp] * 6 + [vp]
+    lib.bm_assemble_reduced.restype = ctypes.c_int
+    lib.bm_assemble_reduced.argtypes = [ctypes.POINTER(bm_qp_desc)] + [dp] * 11 + [vp]
     lib.bm_server_request_bytes.restype = sz
     lib.bm_server_request_bytes.argtypes = [ctypes.POINTER(bm_server_desc), ctypes.POINTER(bm_request)]
     lib.bm_server_create.restype = ctypes.c_int
@@ -543,3 +551,27 @@ class BranchKKTServer:
             self.close()
         except Exception:
             pass
+
+
+# --------------------------------------------------------------------------
+# Assembly front end (include/bm.h, "Assembly front end")
+
+def bm_assemble_reduced(qp: dict, stream=None) -> dict:
+    """K = P + tau I + delta^{-1} A^T A + G^T (W + delta I)^{-1} G of a
+    branch-MPC QP (device tensors A, B, q, rw, r0w, w, w0 and the scalars of
+    bmgen.generate_qp's layout) in the D, E, C, R layout of bm_factor."""
+    import torch
+    S, N, nx, nu = int(qp["S"]), int(qp["N"]), int(qp["nx"]), int(qp["nu"])
+    nb = nx + nu
+    dev = qp["A"].device
+    D = torch.empty((S, N, nb, nb), dtype=torch.float64, device=dev)
+    E = torch.empty((S, max(N - 1, 0), nb, nb), dtype=torch.float64, device=dev)
+    C = torch.empty((S, nu, nb), dtype=torch.float64, device=dev)
+    R = torch.empty((nu, nu), dtype=torch.float64, device=dev)
+    desc = bm_qp_desc(S, N, nx, nu, float(qp["tau"]), float(qp["delta"]))
+    _check(_load().bm_assemble_reduced(ctypes.byref(desc), _ptr(qp["A"], "A"), _ptr(qp["B"], "B"),
+                                       _ptr(qp["q"], "q"), _ptr(qp["rw"], "rw"), _ptr(qp["r0w"], "r0w"),
+                                       _ptr(qp["w"], "w"), _ptr(qp["w0"], "w0"), _ptr(D, "D"),
+                                       _ptr(E, "E") if N > 1 else None, _ptr(C, "C"), _ptr(R, "R"),
+                                       _stream(stream)), "bm_assemble_reduced")
+    return {"D": D, "E": E, "C": C, "R": R, "S": S, "N": N, "nb": nb, "nr": nu}
