@@ -114,6 +114,44 @@ def abs_kx(D, E, C, R, x) -> np.ndarray:
     return np.concatenate([out.reshape(-1), root])
 
 
+def residual_rows(D, E, C, R, x, r, rows) -> dict:
+    """rho_i = r_i - (K x)_i and omega_i = |rho_i| / (|K||x| + |r|)_i for a
+    set of row indices of K only (natural order), each row formed from the
+    blocks it touches (Eq. root_coupled_matrix): for systems too large to
+    check whole on the host."""
+    D, E, C, R, x, r = (_f64(a) for a in (D, E, C, R, x, r))
+    S, N, nb, _ = D.shape
+    nr = R.shape[0]
+    n0 = S * N * nb
+    rows = np.asarray(rows, dtype=np.int64)
+    rho = np.zeros(rows.size)
+    den = np.zeros(rows.size)
+    for t, g in enumerate(rows):
+        if g < n0:
+            s, rem = divmod(int(g), N * nb)
+            k, i = divmod(rem, nb)
+            xs = x[s * N * nb:(s + 1) * N * nb].reshape(N, nb)
+            Dk = D[s, k]
+            row = np.array([Dk[i, j] if j <= i else Dk[j, i] for j in range(nb)])
+            terms = [row * xs[k]]
+            if k > 0:
+                terms.append(E[s, k - 1][i] * xs[k - 1])          # block (k, k-1)
+            if k + 1 < N:
+                terms.append(E[s, k][:, i] * xs[k + 1])           # block (k, k+1) = E^T
+            if k == 0:
+                terms.append(C[s][:, i] * x[n0:])                 # block (1, root) = C^T
+        else:
+            c = int(g) - n0
+            row = np.array([R[c, j] if j <= c else R[j, c] for j in range(nr)])
+            terms = [row * x[n0:]] + [C[s][c] * x[s * N * nb:s * N * nb + nb] for s in range(S)]
+        prod = np.concatenate(terms)
+        rho[t] = r[g] - prod.sum()
+        den[t] = np.abs(prod).sum() + abs(r[g])
+    with np.errstate(divide="ignore", invalid="ignore"):
+        om = np.where(den > 0, np.abs(rho) / np.where(den > 0, den, 1.0), np.where(rho != 0, np.inf, 0.0))
+    return {"rho": rho, "omega": float(om.max()) if om.size else 0.0}
+
+
 def residual(D, E, C, R, x, r, nthreads: int = 0) -> dict:
     """rho = r - K x in FP64, the normwise backward error
     eta = ||rho||_inf / (||K||_inf ||x||_inf + ||r||_inf), the componentwise

@@ -382,3 +382,16 @@ def test_pins_detect_wrong_gamma_start():
     gold = _read_golden("gamma7.txt")[0]
     want = [int(t) for t in gold.replace("|", " ").split()]
     assert gamma_wrong(7) != want
+
+
+@pytest.mark.parametrize("S,N,nb,nr", CASES[:6])
+def test_residual_rows_matches_dense_rows(S, N, nb, nr):
+    d = small(S, N, nb, nr, seed=13 * S + N, barrier=(-2, 2))
+    g = np.random.default_rng(S * N)
+    x = g.standard_normal(S * N * nb + nr)
+    K = dense.assemble_system(d["D"], d["E"], d["C"], d["R"])
+    rows = np.arange(K.shape[0])
+    got = natural.residual_rows(d["D"], d["E"], d["C"], d["R"], x, d["r"], rows)
+    assert np.allclose(got["rho"], d["r"] - K @ x, rtol=1e-12, atol=1e-12 * np.abs(K @ x).max())
+    want = (np.abs(d["r"] - K @ x) / (np.abs(K) @ np.abs(x) + np.abs(d["r"]))).max()
+    assert got["omega"] == pytest.approx(want, rel=1e-9)
