@@ -715,6 +715,26 @@ def run_gpu(args):
         del x64
     launches_per_step = solver.launches_per_step()
     fmean = statistics.mean(fac_ms)
+    # minimum bytes of one factor: A (D, E, C, R in FP64) read once, L (three
+    # blocks per stage, FP64 or FP32) written once
+    wbytes = 8 if args.precision == "fp64" else 4
+    a_bytes = 8 * (w.S * (2 * w.N - 1) * w.nb * w.nb + w.S * w.nr * w.nb + w.nr * w.nr)
+    l_bytes = wbytes * 3 * w.S * w.N * w.nb * w.nb
+    factor_gbs = (a_bytes + l_bytes) / (fmean * 1e-3) / 1e9
+    # the same steps with L2 left warm (no flush between steps)
+    warm = []
+    for _ in range(min(args.steps, 1000)):
+        a_, b_, c_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True), \
+            torch.cuda.Event(enable_timing=True)
+        a_.record(stream)
+        solver.factor(g["D"], g["E"], g["C"], g["R"])
+        b_.record(stream)
+        solver.solve(g["r"], x)
+        c_.record(stream)
+        warm.append((a_, b_, c_))
+    torch.cuda.synchronize()
+    warm_fac = statistics.median(a_.elapsed_time(b_) for a_, b_, _ in warm)
+    warm_sol = statistics.median(b_.elapsed_time(c_) for _, b_, c_ in warm)
     mhz = _peaks()[0].get("sm_max_mhz", 2070.0)
     if args.precision == "fp64":
         peak_alu = fp64_peak_gflops()
@@ -733,6 +753,11 @@ def run_gpu(args):
                    "precision": args.precision, "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "factor_us": fmean * 1e3, "solve_us": statistics.mean(sol_ms) * 1e3,
+        "factor_us_median": statistics.median(fac_ms) * 1e3, "solve_us_median": statistics.median(sol_ms) * 1e3,
+        "l2_warm": {"factor_us_median": warm_fac * 1e3, "solve_us_median": warm_sol * 1e3,
+                    "us_per_kkt": (warm_fac + warm_sol) * 1e3, "steps": len(warm)},
+        "factor_hbm": {"algorithmic_bytes": a_bytes + l_bytes, "achieved_gbs": factor_gbs,
+                       "frac_of_measured_hbm": factor_gbs / _peaks()[0]["hbm_gbs"]},
         "us_per_kkt": ms_per_step * 1e3, **meas,
         "forward_error_vs_fp64": fwd_vs_fp64, "refinement_steps": info.get("iters"),
         "device_status": info["name"],
@@ -753,6 +778,10 @@ def run_gpu(args):
         line["cpu_baseline"] = {"value": fl["total"] / sec / 1e9, "unit": "GFLOP/s", "cores": threads,
                                 "kind": "oracle",
                                 "sample": "full workload factor+solve x%d (%.1f s)" % (reps, sec * reps)}
+        sec1, _, reps1 = time_oracle(sysd, min(3.0, args.ref_budget), min_reps=1, nthreads=1)
+        line["cpu_baseline_single_thread"] = {"value": fl["total"] / sec1 / 1e9, "unit": "GFLOP/s", "cores": 1,
+                                              "kind": "oracle", "us_per_kkt": sec1 * 1e6,
+                                              "sample": "full workload factor+solve x%d" % reps1}
     solver.close()
     if args.precision == "fp64" and not args.no_fp32ir_compare:
         # the FP32-tail + FP64-refinement path on the same system, same timing
