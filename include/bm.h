@@ -306,6 +306,16 @@ bm_status bm_batch_schedule(bm_batch b, int *threads_per_cta, int *ctas_per_sm, 
 /* Frees everything the batch owns. */
 void bm_batch_destroy(bm_batch b);
 
+/*
+ * Test entry of the bounded device wait that the batched factor uses (the
+ * paper has no counterpart): one warp waits, with that same wait, on a
+ * counter that nothing increments; the wait gives up after limit_cycles SM
+ * clock cycles (1 .. 2^33) and records BM_ERR_TIMEOUT, which this call
+ * returns after synchronizing stream. Any other return value means the wait
+ * did not behave. Allocates and frees 256 bytes of device memory.
+ */
+bm_status bm_test_bounded_wait(unsigned long long limit_cycles, void *stream);
+
 /* Frees everything the handle owns (synchronizes its internal stream). */
 void bm_destroy(bm_handle h);
 

@@ -8,7 +8,7 @@ library was not built (``python -c "import __graft_entry__ as g; g.build()"``).
 """
 from .bm import (BATCH_NB, BranchKKTBatch, bm_batch_analyze, bm_batch_destroy, bm_batch_factor, bm_batch_query,
                  bm_batch_schedule, bm_batch_solve, bm_batch_workspace_bytes)
-from .bm import bm_assemble_reduced
+from .bm import bm_assemble_reduced, bm_test_bounded_wait
 from .bm import (BM_REQ_HOST_IO, BM_SERVE_MAX_RHS, BranchKKTServer, bm_server_create, bm_server_destroy,
                  bm_server_get_stats, bm_server_poll, bm_server_request_bytes, bm_server_submit, make_server_desc)
 from .bm import (BM_FLAG_NO_GRAPH, BM_PREC_FP32_IR, BM_PREC_FP64, BMError, BranchKKTSolver, bm_analyze,
@@ -21,4 +21,4 @@ __all__ = ["BranchKKTBatch", "BATCH_NB", "bm_batch_analyze", "bm_batch_factor", 
            "bm_version", "bm_status_string", "library_path", "BM_PREC_FP64", "BM_PREC_FP32_IR",
            "BM_FLAG_NO_GRAPH", "BranchKKTServer", "BM_REQ_HOST_IO", "BM_SERVE_MAX_RHS", "bm_server_create",
            "bm_server_destroy", "bm_server_get_stats", "bm_server_poll", "bm_server_request_bytes",
-           "bm_server_submit", "make_server_desc", "bm_assemble_reduced"]
+           "bm_server_submit", "make_server_desc", "bm_assemble_reduced", "bm_test_bounded_wait"]

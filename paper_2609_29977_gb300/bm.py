@@ -28,7 +28,7 @@ EXPORTED_SYMBOLS = ("bm_version", "bm_status_string", "bm_workspace_bytes", "bm_
                     "bm_batch_analyze", "bm_batch_factor", "bm_batch_solve", "bm_batch_query",
                     "bm_batch_schedule", "bm_batch_destroy", "bm_server_request_bytes", "bm_server_create",
                     "bm_server_submit", "bm_server_poll", "bm_server_get_stats", "bm_server_destroy",
-                    "bm_assemble_reduced")
+                    "bm_assemble_reduced", "bm_test_bounded_wait")
 BATCH_NB = (4, 6, 12, 24, 48)
 BM_NOALLOC_SCRATCH_BYTES = 32 << 20
 BM_SERVE_MAX_RHS = 8
@@ -141,6 +141,8 @@ def _load():
     lib.bm_round_to_fp32.argtypes = [dp, dp, ctypes.c_size_t, vp]
     lib.bm_factor_solve_noalloc.restype = ctypes.c_int
     lib.bm_factor_solve_noalloc.argtypes = [ctypes.c_int] * 4 + [dp] * 6 + [vp]
+    lib.bm_test_bounded_wait.restype = ctypes.c_int
+    lib.bm_test_bounded_wait.argtypes = [ctypes.c_ulonglong, vp]
     lib.bm_assemble_reduced.restype = ctypes.c_int
     lib.bm_assemble_reduced.argtypes = [ctypes.POINTER(bm_qp_desc)] + [dp] * 11 + [vp]
     lib.bm_server_request_bytes.restype = sz
@@ -575,3 +577,9 @@ def bm_assemble_reduced(qp: dict, stream=None) -> dict:
                                        _ptr(E, "E") if N > 1 else None, _ptr(C, "C"), _ptr(R, "R"),
                                        _stream(stream)), "bm_assemble_reduced")
     return {"D": D, "E": E, "C": C, "R": R, "S": S, "N": N, "nb": nb, "nr": nu}
+
+
+def bm_test_bounded_wait(limit_cycles: int, stream=None) -> int:
+    """Status left by the batched factor's bounded wait on a counter that
+    nothing increments (BM_ERR_TIMEOUT = 6 when the wait behaves)."""
+    return int(_load().bm_test_bounded_wait(int(limit_cycles), _stream(stream)))

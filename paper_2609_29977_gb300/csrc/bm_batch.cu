@@ -381,10 +381,41 @@ void cache_store(const std::string &key, int threads, int cps) {
   fclose(f);
 }
 
+// One lane waits with the batched factor's bounded wait on a counter that
+// nothing increments: the wait must give up after `limit` cycles and leave
+// BM_ERR_TIMEOUT in the status word (the test of bm_test_bounded_wait).
+__global__ void k_wait_nothing(const unsigned *cnt, unsigned long long limit, Status *st) {
+  wait_count(cnt, 1u, limit, st, (int)threadIdx.x, 0xffffffffu);
+}
+
 }  // namespace
 }  // namespace bm
 
 using namespace bm;
+
+extern "C" bm_status bm_test_bounded_wait(unsigned long long limit_cycles, void *stream) {
+  if (limit_cycles == 0 || limit_cycles > (1ull << 33)) return BM_ERR_INVALID_ARG;   // at most a few seconds
+  cudaStream_t st = (cudaStream_t)stream;
+  void *mem = nullptr;
+  if (cudaMallocAsync(&mem, 256, st) != cudaSuccess) {
+    cudaGetLastError();
+    return BM_ERR_OOM;
+  }
+  unsigned *cnt = (unsigned *)mem;
+  Status *status = (Status *)((char *)mem + 64);
+  Status h{};
+  bm_status rc = BM_ERR_CUDA;
+  if (cudaMemsetAsync(mem, 0, 256, st) == cudaSuccess) {
+    k_wait_nothing<<<1, 32, 0, st>>>(cnt, limit_cycles, status);
+    if (cudaMemcpyAsync(&h, status, sizeof(Status), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+        cudaStreamSynchronize(st) == cudaSuccess)
+      rc = (bm_status)h.code;
+  }
+  cudaFreeAsync(mem, st);
+  cudaStreamSynchronize(st);
+  cudaGetLastError();
+  return rc;
+}
 
 struct bm_batch_s {
   int count = 0;

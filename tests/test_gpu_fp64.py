@@ -257,6 +257,28 @@ def test_fp64_invalid_arguments_are_rejected():
     solver.close()
 
 
+def test_fp64_analyze_reports_allocation_failure():
+    """A workspace far beyond the device's memory: bm_analyze returns
+    BM_ERR_OOM and the context stays usable."""
+    bm = _bm()
+    with pytest.raises(bm.BMError) as e:
+        bm.BranchKKTSolver(40000, 1 << 16, 48, 16)
+    assert e.value.code == 3
+    solver = bm.BranchKKTSolver(2, 4, 3, 2)      # still works afterwards
+    solver.close()
+
+
+def test_bounded_device_wait_times_out():
+    """The bounded wait of the batched factor, on a counter that nothing
+    increments, gives up after its limit (~1 ms here) with BM_ERR_TIMEOUT."""
+    bm = _bm()
+    import time
+    t0 = time.perf_counter()
+    assert bm.bm_test_bounded_wait(2_000_000) == 6
+    assert time.perf_counter() - t0 < 5.0
+    assert bm.bm_test_bounded_wait(0) == 1      # invalid limit
+
+
 def test_fp64_handles_with_different_block_sizes_coexist():
     """Analyzing a small-block handle after a large-block one must not break
     the large one (kernel attributes are process-wide)."""
