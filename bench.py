@@ -82,13 +82,18 @@ def _factor_kernels(N, nb, precision):
 
 
 def _kernel_source_hash():
+    """Hash of every CUDA source that holds device code (host-only files
+    such as the serving runtime cannot change what a kernel does)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2609_29977_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
         if name.endswith((".cu", ".cuh")):
             with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode())
-                h.update(f.read())
+                src = f.read()
+            if b"__global__" not in src and b"__device__" not in src:
+                continue
+            h.update(name.encode())
+            h.update(src)
     return h.hexdigest()[:16]
 
 

@@ -325,7 +325,7 @@ static void retire(bm_server s, Slot &sl, bm_status launch_rc) {
       const Status &v = sl.hs[1 + j];
       c.iters[j] = mixed ? v.iters : 0;
       c.backward_error[j] = mixed ? v.eta : -1.0;
-      // the status word is sticky over the solves of one factor: judge each
+      // the status word is sticky over the solves of one factor: rate each
       // right-hand side by its own backward error
       int code = v.code;
       if (mixed && code == BM_ERR_NOT_CONVERGED) code = v.eta <= s->desc.tol ? BM_OK : BM_ERR_NOT_CONVERGED;
