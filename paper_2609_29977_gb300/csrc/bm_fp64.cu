@@ -482,7 +482,6 @@ cudaError_t f64_prepare(int nb, int nr) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorUnknown;
   if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
-  if (dev >= 0 && dev < 64) done[dev] = true;   // attributes below are idempotent
   nb = nr = 64;
   const int smem = (int)f64_factor_smem(nb, nr);
   cudaError_t e = cudaFuncSetAttribute(k_factor_level, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -498,10 +497,12 @@ cudaError_t f64_prepare(int nb, int nr) {
   e = cudaFuncSetAttribute(k_factor_root, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(((size_t)nr * nr + nr) * sizeof(double)));
   if (e != cudaSuccess) return e;
-  return tail_factor_prepare();
+  e = tail_factor_prepare();
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;   // only once everything was set
+  return e;
 }
 
-// Block sizes with compile-time kernels (bm_fp64_team.cu) use those; any
+// Block sizes with compile-time kernels (bm_tail_factor.cuh) use those; any
 // other nb runs the runtime-size kernels above.
 void f64_launch_factor(const F64View &v, cudaStream_t st) {
   if (tail_nb_supported(v.nb)) {
