@@ -298,7 +298,8 @@ def run_batched(args):
     t0 = time.perf_counter()
     systems = []
     for j, (S, N, nb, nr) in enumerate(shapes):
-        systems.append(bmgen.generate(base.with_shape(S=S, N=N, nb=nb, nr=nr), instance=j, device=dev))
+        d = bmgen.generate(base.with_shape(S=S, N=N, nb=nb, nr=nr), instance=j, device=args.gen_device)
+        systems.append({k: (v.to(dev) if isinstance(v, torch.Tensor) else v) for k, v in d.items()})
     gen_s = time.perf_counter() - t0
     flops = sum(bmgen.method_flops(S, N, nb, nr)["total"] for (S, N, nb, nr) in shapes)
     batch = bm.BranchKKTBatch(shapes, max_refine=args.max_refine, tol=args.tol)
@@ -842,6 +843,7 @@ def main():
     ap.add_argument("--slots", type=int, default=8, help="serving: requests in flight at most")
     ap.add_argument("--serve-budget-gb", type=float, default=160.0, help="serving: HBM arena")
     ap.add_argument("--seed", type=int, default=2000)
+    ap.add_argument("--gen-device", default="cuda", help="batched: where the systems are drawn (cuda or cpu)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
