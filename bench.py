@@ -614,6 +614,70 @@ def run_assembly(args):
     return 0
 
 
+def run_grid(args):
+    """Context sweep over the paper's experiment grid (Sec. V): nb = nr = 16,
+    scenario counts M and horizons N, factor and solve (FP64, or FP32+IR
+    with --precision fp32ir) timed with the
+    paper's protocol (device-resident data, analysis and graph capture
+    excluded, median of 50 after 10 warm-ups; L2 not flushed). Synthetic
+    systems stand in for the paper's quadrotor model (barrier off)."""
+    import torch
+
+    import bmgen
+    import paper_2609_29977_gb300 as bm
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    base = bmgen.WORKLOADS["grid-s100-n160-nb16"]
+    pts = [(m, 30) for m in (20, 60, 100, 140, 200)] + [(100, n) for n in (40, 80, 120, 160)] + [(200, 160)]
+    out = []
+    for m, n in pts:
+        w = base.with_shape(S=m, N=n)
+        d = bmgen.generate(w, device=dev)
+        prec = bm.BM_PREC_FP64 if args.precision == "fp64" else bm.BM_PREC_FP32_IR
+        solver = bm.BranchKKTSolver(m, n, w.nb, w.nr, precision=prec, max_refine=args.max_refine, tol=args.tol)
+        x = torch.empty_like(d["r"])
+        for _ in range(10):
+            solver.factor(d["D"], d["E"], d["C"], d["R"])
+            solver.solve(d["r"], x)
+        fac, sol = [], []
+        for _ in range(50):
+            a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a.record(stream)
+            solver.factor(d["D"], d["E"], d["C"], d["R"])
+            b.record(stream)
+            solver.solve(d["r"], x)
+            c.record(stream)
+            torch.cuda.synchronize()
+            fac.append(a.elapsed_time(b))
+            sol.append(b.elapsed_time(c))
+        info = solver.query()
+        solver.close()
+        meas = gpu_residual_measures(d, x)
+        out.append({"M": m, "N": n, "factor_ms": statistics.median(fac), "solve_ms": statistics.median(sol),
+                    "status": info["name"], "omega": meas["omega"], "refinement_steps": info["iters"]})
+        del d, x
+    at = {(p["M"], p["N"]): p for p in out}
+    line = {
+        "metric": "paper grid (nb = nr = 16): %s factor and solve ms per point, median of 50" % args.precision,
+        "value": at[(100, 160)]["factor_ms"], "unit": "ms (factor, M=100, N=160)", "n_gpus": 1, "steps": 50,
+        "warmup": 10, "ms_per_step": at[(100, 160)]["factor_ms"] + at[(100, 160)]["solve_ms"],
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic (seeded MPC-shaped generator, barrier off)",
+        "config": {"workload": "paper-grid-nb16", "points": len(out), "l2": "not flushed (the paper's protocol)"},
+        "points": out,
+        "factor_growth_N40_to_160_at_M100": at[(100, 160)]["factor_ms"] / at[(100, 40)]["factor_ms"],
+        "solve_growth_N40_to_160_at_M100": at[(100, 160)]["solve_ms"] / at[(100, 40)]["solve_ms"],
+        "paper_context_rtx5090": {"factor_ms_N30_M20_to_200": [0.15, 0.35], "solve_ms_N30_M20_to_200": [0.10, 0.16],
+                                  "factor_ms_M100_N160": "< 1", "solve_ms_M100_N160": "< 0.35",
+                                  "growth_N40_to_160_at_M100": {"factor": 3.1, "solve": 2.3}},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_gpu(args):
     import torch
 
@@ -853,6 +917,8 @@ def main():
         return run_serving(args)
     if args.workload.startswith("assembly"):
         return run_assembly(args)
+    if args.workload.startswith("paper-grid"):
+        return run_grid(args)
     return run_gpu(args)
 
 
