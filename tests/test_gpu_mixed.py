@@ -165,8 +165,9 @@ def test_mixed_not_spd_is_reported():
 def test_mixed_workload_full_size():
     """The mixed-precision workload at full size (S=512, N=128, nb=24, nr=8,
     barrier 10^U[-6,6]) at the 1e-10 target. Its root Schur complement
-    R - sum_i U_i cancels by ~1e9 (the generator makes it exactly R0 = nr I),
-    more than FP32 tail factors can carry, so refinement may not reach the
+    R - sum_i U_i cancels by 2.8e4 in the 2-norm (the generator makes it
+    exactly R0 = nr I) while FP32 tail factors give each U_i only to about
+    1e-5, so the root block is wrong by O(1) and refinement may not reach the
     target: the path must then say so (BM_ERR_NOT_CONVERGED, or BM_ERR_NOT_SPD
     at the root) instead of reporting a false success, and whatever it
     reports must hold against the oracle's componentwise backward error."""
