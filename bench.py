@@ -702,7 +702,7 @@ def run_gpu(args):
     g = {k: v.to(dev) for k, v in sysd.items() if isinstance(v, torch.Tensor)}
     fl = bmgen.method_flops(w.S, w.N, w.nb, w.nr)
     solver = bm.BranchKKTSolver(w.S, w.N, w.nb, w.nr, precision=prec, max_refine=args.max_refine,
-                                tol=args.tol)
+                                tol=args.tol, flags=bm.BM_FLAG_NO_GRAPH if args.direct else 0)
     x = torch.empty_like(g["r"])
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -772,7 +772,7 @@ def run_gpu(args):
 
     meas = gpu_residual_measures(g, x)
     fwd_vs_fp64 = None
-    if args.precision != "fp64":
+    if args.precision != "fp64" and not args.no_fp64_compare:
         # the error of the mixed result against the FP64 path's solution
         ref = bm.BranchKKTSolver(w.S, w.N, w.nb, w.nr)
         ref.factor(g["D"], g["E"], g["C"], g["R"])
@@ -780,7 +780,10 @@ def run_gpu(args):
         fwd_vs_fp64 = float((x - x64).abs().max() / x64.abs().max())
         ref.close()
         del x64
-    launches_per_step = solver.launches_per_step()
+    # a captured solve stops its refinement loop after the last iteration that
+    # runs; directly launched, every unrolled iteration is a launch
+    graph_loop = prec == bm.BM_PREC_FP32_IR and not args.direct
+    launches_per_step = solver.launches_per_step(info.get("iters") if graph_loop else None)
     fmean = statistics.mean(fac_ms)
     # minimum bytes of one factor: A (D, E, C, R in FP64) read once, L (three
     # blocks per stage, FP64 or FP32) written once
@@ -818,6 +821,7 @@ def run_gpu(args):
         "data": "synthetic (seeded MPC-shaped generator; the paper's quadrotor data are not available)",
         "config": {"workload": w.name, "S": w.S, "N": w.N, "nb": w.nb, "nr": w.nr,
                    "precision": args.precision, "l2": "flushed between timed steps (256 MiB write)",
+                   "launch": "direct" if args.direct else "graph",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "factor_us": fmean * 1e3, "solve_us": statistics.mean(sol_ms) * 1e3,
         "factor_us_median": statistics.median(fac_ms) * 1e3, "solve_us_median": statistics.median(sol_ms) * 1e3,
@@ -898,8 +902,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shape", default="", help="S,N,nb,nr override of the workload's shape (profiling)")
     ap.add_argument("--batch-count", type=int, default=256, help="systems in the batched workload")
-    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip the FP64 reference run of the batched and mixed-precision lines")
     ap.add_argument("--no-fp32ir-compare", action="store_true")
+    ap.add_argument("--direct", action="store_true",
+                    help="launch the kernels directly instead of replaying CUDA graphs (for ncu launch lists: ncu "
+                         "does not list the kernels inside a graph's conditional refinement loop)")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean Poisson arrivals per second")
     ap.add_argument("--requests", type=int, default=200, help="serving: requests per run")
     ap.add_argument("--pool", type=int, default=24, help="serving: distinct small systems")

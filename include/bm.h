@@ -132,7 +132,11 @@ bm_status bm_factor(bm_handle h, const double *D, const double *E, const double 
  *     omega = max_i |r - K x|_i / (|K| |x| + |r|)_i     (Oettli-Prager)
  * is <= tol. It reports BM_ERR_NOT_CONVERGED (x = the last iterate) after
  * max_refine corrections, or earlier once omega fails to halve from one
- * correction to the next (stalled or diverging refinement). Asynchronous.
+ * correction to the next (stalled or diverging refinement). In the captured
+ * graph the refinement iterations are a conditional loop that ends on the
+ * device after the last iteration that runs; with BM_FLAG_NO_GRAPH the
+ * max_refine + 1 iterations are launched and those after the stopping test
+ * return at once. Both give bitwise the same x. Asynchronous.
  * Errors: BM_ERR_INVALID_ARG, BM_ERR_NOT_FACTORED, BM_ERR_CUDA.
  */
 bm_status bm_solve(bm_handle h, const double *r, double *x, void *stream);

@@ -285,9 +285,12 @@ class BranchKKTSolver:
         bm_solve(self.h, r, x, stream)
         return x
 
-    def launches_per_step(self) -> int:
-        """Kernels one bm_factor + one bm_solve launch (an upper bound on the
-        mixed path, whose refinement launches exit at once after convergence)."""
+    def launches_per_step(self, iters=None) -> int:
+        """Kernels one bm_factor + one bm_solve launch. On the mixed path the
+        solve launches three kernels per refinement iteration: pass the
+        corrections of the solve (``query()["iters"]``) for the count of a
+        captured graph, whose loop stops after the last iteration that runs;
+        without it the count is the unrolled direct-launch bound."""
         S, N, nb, nr = self.shape
         if self.desc.precision == BM_PREC_FP32_IR:
             Lc = (N - 1).bit_length() if N > 1 else 0
@@ -296,7 +299,8 @@ class BranchKKTSolver:
                 if (N // 2 if lvl == 0 else ((N - 1) >> lvl) + 1) <= 4:
                     top = lvl
                     break
-            return (top + 2) + 3 * (self.desc.max_refine + 1)
+            runs = self.desc.max_refine + 1 if iters is None else min(int(iters), self.desc.max_refine) + 1
+            return (top + 2) + 3 * runs
         Lc = (N - 1).bit_length() if N > 1 else 0
         if nb not in (2, 3, 4, 6, 8, 12, 16, 24, 32, 48):
             return (Lc + 2) + (2 * Lc + 3)

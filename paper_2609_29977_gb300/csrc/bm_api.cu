@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <new>
+#include <type_traits>
 
 #include "bm_internal.cuh"
 
@@ -26,8 +27,11 @@ MixedState *mixed_create(int S, int N, int nb, int nr, void *base, size_t bytes,
 void mixed_destroy(MixedState *m);
 void mixed_launch_factor(MixedState *m, const double *D, const double *E, const double *C,
                          const double *R, cudaStream_t st);
-void mixed_launch_solve(MixedState *m, const double *r, double *x, int max_refine, double tol,
-                        cudaStream_t st);
+// body_st non-null: st is capturing, and the refinement loop becomes a
+// conditional graph node whose body is captured from body_st (programmatic
+// launches inside the body when body_pdl is set).
+cudaError_t mixed_launch_solve(MixedState *m, const double *r, double *x, int max_refine, double tol,
+                               cudaStream_t st, cudaStream_t body_st, bool body_pdl);
 void mixed_launch_export(MixedState *m, double *Ld, double *Ll, double *Lr, double *F, double *LR,
                          cudaStream_t st);
 }  // namespace bm
@@ -51,7 +55,9 @@ struct bm_handle_s {
   Status *status = nullptr;
   unsigned *tickets = nullptr;
   MixedState *mixed = nullptr;
-  cudaStream_t cap = nullptr;
+  cudaStream_t cap = nullptr;      // private capture stream
+  cudaStream_t cap_body = nullptr; // captures the body of the refinement loop (mixed path)
+  bool loop_pdl = true;            // programmatic launches inside that body (cleared if they do not instantiate)
   GraphSlot gfac, gsol;
   bool factored = false;
   // host-entry staging (allocated on first use)
@@ -171,6 +177,8 @@ bm_status analyze_impl(const bm_desc *desc, void *mem, size_t bytes, cudaStream_
   }
   if (!light) {
     if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) goto cuda_fail;
+    if (h->mixed && cudaStreamCreateWithFlags(&h->cap_body, cudaStreamNonBlocking) != cudaSuccess)
+      goto cuda_fail;
     if (cudaDeviceSynchronize() != cudaSuccess) goto cuda_fail;
   }
   *out = h;
@@ -179,6 +187,7 @@ cuda_fail:
   cudaGetLastError();
   if (h->mixed) mixed_destroy(h->mixed);
   if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->cap_body) cudaStreamDestroy(h->cap_body);
   if (h->owns_pool) cudaFree(h->pool);
   delete h;
   return BM_ERR_CUDA;
@@ -197,6 +206,7 @@ void release_impl(bm_handle h) {
   if (h->gsol.exec) cudaGraphExecDestroy(h->gsol.exec);
   if (h->mixed) mixed_destroy(h->mixed);
   if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->cap_body) cudaStreamDestroy(h->cap_body);
   if (h->sD) cudaFree(h->sD);
   if (h->owns_pool) cudaFree(h->pool);
   delete h;
@@ -213,25 +223,41 @@ static bool key_match(const GraphSlot &g, const void *const *k, int n) {
   return true;
 }
 
-// Runs body(stream) either directly or through the graph cached in slot
+// body(stream, capturing) issues the work; it returns void (errors are read
+// from the runtime's last error) or a cudaError_t.
+template <typename Body>
+static cudaError_t call_body(Body &body, cudaStream_t s, bool capturing) {
+  if constexpr (std::is_void_v<decltype(body(s, capturing))>) {
+    body(s, capturing);
+    return cudaPeekAtLastError();
+  } else {
+    return body(s, capturing);
+  }
+}
+
+// Runs body either directly or through the graph cached in slot
 // (re-captured on the handle's private stream when the pointers change).
+// A capture during which any call failed is discarded.
 template <typename Body>
 static bm_status run(bm_handle h, GraphSlot &slot, const void *const *key, int nkey, cudaStream_t st,
                      Body body) {
   if (h->desc.flags & BM_FLAG_NO_GRAPH) {
-    body(st);
-    return cudaGetLastError() == cudaSuccess ? BM_OK : BM_ERR_CUDA;
+    const cudaError_t e = call_body(body, st, false);
+    cudaGetLastError();
+    return e == cudaSuccess ? BM_OK : BM_ERR_CUDA;
   }
   if (!key_match(slot, key, nkey)) {
     if (slot.exec) {
       cudaGraphExecDestroy(slot.exec);
       slot.exec = nullptr;
     }
+    cudaGetLastError();
     if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return BM_ERR_CUDA;
-    body(h->cap);
+    const cudaError_t eb = call_body(body, h->cap, true);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->cap, &g);
-    if (e != cudaSuccess || !g) {
+    if (eb != cudaSuccess || e != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
       cudaGetLastError();
       return BM_ERR_CUDA;
     }
@@ -257,14 +283,14 @@ extern "C" bm_status bm_factor(bm_handle h, const double *D, const double *E, co
   if (h->mixed) {
     MixedState *m = h->mixed;
     Status *status = h->status;
-    s = run(h, h->gfac, key, 4, st, [&](cudaStream_t cs) {
+    s = run(h, h->gfac, key, 4, st, [&](cudaStream_t cs, bool) {
       cudaMemsetAsync(status, 0, sizeof(Status), cs);
       mixed_launch_factor(m, D, E, C, R, cs);
     });
   } else {
     F64View v = h->v;
     v.D = D; v.E = E; v.C = C; v.R = R;
-    s = run(h, h->gfac, key, 4, st, [&](cudaStream_t cs) {
+    s = run(h, h->gfac, key, 4, st, [&](cudaStream_t cs, bool) {
       cudaMemsetAsync(v.status, 0, sizeof(Status), cs);
       f64_launch_factor(v, cs);
     });
@@ -285,12 +311,23 @@ extern "C" bm_status bm_solve(bm_handle h, const double *r, double *x, void *str
     const double tol = h->desc.tol;
     // the refinement residual reads the factor's inputs: key on them as well
     const void *key[6] = {r, x, h->gfac.key[0], h->gfac.key[1], h->gfac.key[2], h->gfac.key[3]};
-    return run(h, h->gsol, key, 6, st, [&](cudaStream_t cs) { mixed_launch_solve(m, r, x, mr, tol, cs); });
+    cudaStream_t body_st = h->cap_body;
+    auto body = [&](cudaStream_t cs, bool capturing) {
+      return mixed_launch_solve(m, r, x, mr, tol, cs, capturing ? body_st : nullptr, h->loop_pdl);
+    };
+    bm_status s = run(h, h->gsol, key, 6, st, body);
+    if (s == BM_ERR_CUDA && h->loop_pdl && !(h->desc.flags & BM_FLAG_NO_GRAPH)) {
+      // a graph whose loop body chains its kernels programmatically may not
+      // instantiate on every driver: capture the body with plain launches
+      h->loop_pdl = false;
+      s = run(h, h->gsol, key, 6, st, body);
+    }
+    return s;
   }
   F64View v = h->v;
   double *r0t = h->r0t;
   const void *key[2] = {r, x};
-  return run(h, h->gsol, key, 2, st, [&](cudaStream_t cs) { f64_launch_solve(v, r, x, r0t, cs); });
+  return run(h, h->gsol, key, 2, st, [&](cudaStream_t cs, bool) { f64_launch_solve(v, r, x, r0t, cs); });
 }
 
 extern "C" bm_status bm_query(bm_handle h, void *stream, bm_info *info) {

@@ -15,9 +15,17 @@
 //   when omega fails to halve from one iteration to the next.
 // Each iteration is three launches: forward tail substitution whose last CTA
 // does the root step, backward tail substitution fused with x += d, and the
-// residual whose last CTA applies the stopping test and raises a device flag
-// once it holds; every later launch checks the flag first and returns, so the
-// whole unrolled loop is one CUDA graph with no host round trip.
+// residual whose last CTA applies the stopping test.
+//  * In a captured graph the iterations are the body of one conditional
+//    WHILE node: the forward kernel first sets the loop condition to 0, and
+//    the residual's last CTA sets it back to 1 only when another iteration
+//    is to run, so the loop ends on the device after the last useful
+//    iteration (at most max_refine + 1 bodies) with no host round trip.
+//  * Launched directly, the max_refine + 1 iterations are unrolled; once the
+//    stopping test holds it raises a device flag, and every later launch
+//    checks the flag first and returns.
+// Both forms run the same kernels on the same data: the results are
+// bitwise identical.
 #include <cuda_runtime.h>
 
 #include <new>
@@ -28,15 +36,22 @@ namespace bm {
 namespace {
 using namespace mx;
 
+// iter >= 0: a directly launched iteration; iter < 0: the body of a graph
+// loop, whose iteration index is read from the control block and whose
+// condition handle is cond.
 template <int NB>
-__global__ void __launch_bounds__(256) k_mixed_fwd(MixedState m, const double *__restrict__ rhs, double *x, int iter,
-                                                    int CS) {
+__global__ void __launch_bounds__(256) k_mixed_fwd(MixedState m, const double *__restrict__ r, double *x, int iter,
+                                                    int CS, cudaGraphConditionalHandle cond) {
   __shared__ float sY[MCfg<NB>::TEAMS][NB];
   __shared__ double sR[64 * 64 + 64 + 64];
   pdl_wait();
+  // the loop stops after this iteration unless its stopping test says otherwise
+  if (iter < 0 && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
   if (ir_done(m.ctl)) return;
+  const int it = ir_iter(m.ctl, iter);
+  const double *rhs = it == 0 ? r : m.rho;
   fwd_tail<NB>(m, rhs, blockIdx.x / CS, (int)cluster_rank(), CS, sY);
-  if (last_cta(&m.tickets[2], gridDim.x)) root_step<NB>(m, rhs, x, iter, sR);
+  if (last_cta(&m.tickets[2], gridDim.x)) root_step<NB>(m, rhs, x, it, sR);
 }
 
 template <int NB>
@@ -44,7 +59,7 @@ __global__ void __launch_bounds__(256) k_mixed_bwd(MixedState m, double *x, int 
   __shared__ float sX[MCfg<NB>::TEAMS][NB];
   pdl_wait();
   if (ir_done(m.ctl)) return;
-  bwd_tail<NB>(m, x, iter, blockIdx.x / CS, (int)cluster_rank(), CS, sX);
+  bwd_tail<NB>(m, x, ir_iter(m.ctl, iter), blockIdx.x / CS, (int)cluster_rank(), CS, sX);
 }
 
 // rho = r - K x in FP64 and the componentwise backward error of the
@@ -54,10 +69,11 @@ __global__ void __launch_bounds__(256) k_mixed_bwd(MixedState m, double *x, int 
 template <int NB>
 __global__ void __launch_bounds__(256) k_mixed_residual(MixedState m, const double *__restrict__ r,
                                                          const double *__restrict__ x, int iter, int max_iter,
-                                                         double tol) {
+                                                         double tol, cudaGraphConditionalHandle cond) {
   __shared__ unsigned sroot;
   pdl_wait();
   if (ir_done(m.ctl)) return;
+  const int it = ir_iter(m.ctl, iter);
   const long nrow = (long)m.S * m.N * NB;
   float om = 0.0f;
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < nrow; e += (long)gridDim.x * blockDim.x) {
@@ -76,7 +92,10 @@ __global__ void __launch_bounds__(256) k_mixed_residual(MixedState m, const doub
   }
   __syncthreads();
   if (threadIdx.x == 0 && sroot) atomicMax(&m.ctl->wmax, sroot);
-  if (last_cta(&m.tickets[3], gridDim.x) && threadIdx.x == 0) ir_stop(m, 0.0f, iter, max_iter, tol);
+  if (last_cta(&m.tickets[3], gridDim.x) && threadIdx.x == 0) {
+    const bool more = ir_stop(m, 0.0f, it, max_iter, tol);
+    if (iter < 0 && more) cudaGraphSetConditional(cond, 1u);
+  }
 }
 
 // Widen the FP32 tail factor for export.
@@ -91,8 +110,10 @@ int pick_cluster(int S) {
   return cs;
 }
 
+// pdl: allow programmatic dependent launch after the previous kernel.
 template <typename... KArgs, typename... Args>
-void launch_cluster(void (*kern)(KArgs...), unsigned grid, unsigned block, int CS, cudaStream_t st, Args... args) {
+void launch_cluster(void (*kern)(KArgs...), unsigned grid, unsigned block, int CS, bool pdl, cudaStream_t st,
+                    Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);
@@ -104,25 +125,79 @@ void launch_cluster(void (*kern)(KArgs...), unsigned grid, unsigned block, int C
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  attr[1].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
   cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
+template <typename... KArgs, typename... Args>
+void launch_plain(void (*kern)(KArgs...), unsigned grid, unsigned block, bool pdl, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+// One iteration (iter >= 0), or the body of the graph loop (iter = -1).
 template <int NB>
 void launch_iteration(const MixedState &m, const double *r, double *x, int iter, int max_iter, double tol,
-                      cudaStream_t st) {
+                      cudaStream_t st, cudaGraphConditionalHandle cond, bool pdl) {
   const int CS = pick_cluster(m.S);
   const unsigned grid = (unsigned)(m.S * CS);
-  const double *rhs = iter == 0 ? r : m.rho;
-  launch_cluster(k_mixed_fwd<NB>, grid, 256, CS, st, m, rhs, x, iter, CS);
-  launch_cluster(k_mixed_bwd<NB>, grid, 256, CS, st, m, x, iter, CS);
+  launch_cluster(k_mixed_fwd<NB>, grid, 256, CS, pdl, st, m, r, x, iter, CS, cond);
+  launch_cluster(k_mixed_bwd<NB>, grid, 256, CS, pdl, st, m, x, iter, CS);
   const long rows = (long)m.S * m.N * NB;
   long blocks = (rows + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
   if (blocks < m.nr) blocks = m.nr;
-  launch_pdl(k_mixed_residual<NB>, (unsigned)blocks, 256, 0, st, m, r, (const double *)x, iter, max_iter, tol);
+  launch_plain(k_mixed_residual<NB>, (unsigned)blocks, 256, pdl, st, m, r, (const double *)x, iter, max_iter, tol,
+               cond);
+}
+
+// Adds the refinement loop to the graph being captured on st: a conditional
+// WHILE node (condition 1 at every graph launch) after st's current
+// dependencies, whose body graph is captured from body_st (with programmatic
+// launches between its kernels when body_pdl is set).
+template <int NB>
+cudaError_t capture_loop(const MixedState &m, const double *r, double *x, int max_iter, double tol,
+                         cudaStream_t st, cudaStream_t body_st, bool body_pdl) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  const cudaGraphEdgeData *edges = nullptr;
+  size_t ndeps = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &edges, &ndeps);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusActive || !g) return cudaErrorStreamCaptureInvalidated;
+  cudaGraphConditionalHandle cond = 0;
+  e = cudaGraphConditionalHandleCreate(&cond, g, 1u, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = cond;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  e = cudaGraphAddNode(&node, g, deps, edges, ndeps, &p);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  e = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamBeginCaptureToGraph(body_st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  launch_iteration<NB>(m, r, x, -1, max_iter, tol, body_st, cond, body_pdl);
+  const cudaError_t el = cudaPeekAtLastError();
+  cudaGraph_t out = nullptr;
+  e = cudaStreamEndCapture(body_st, &out);
+  return el != cudaSuccess ? el : e;
 }
 
 }  // namespace
@@ -197,22 +272,34 @@ void mixed_launch_factor(MixedState *m, const double *D, const double *E, const 
   f64_launch_factor_root_raw(m->S, m->nr, m->U, R, m->Rt, m->LR, m->tickets, m->status, st);
 }
 
-void mixed_launch_solve(MixedState *m, const double *r, double *x, int max_refine, double tol, cudaStream_t st) {
+cudaError_t mixed_launch_solve(MixedState *m, const double *r, double *x, int max_refine, double tol,
+                               cudaStream_t st, cudaStream_t body_st, bool body_pdl) {
   // reset the per-solve control words
-  cudaMemsetAsync(m->ctl, 0, sizeof(IRCtl), st);
+  cudaError_t e = cudaMemsetAsync(m->ctl, 0, sizeof(IRCtl), st);
+  if (e != cudaSuccess) return e;
+  if (body_st) {
+    switch (m->nb) {
+#define X(n) \
+  case n:    \
+    return capture_loop<n>(*m, r, x, max_refine, tol, st, body_st, body_pdl);
+      BM_TAIL_NB_LIST(X)
+#undef X
+    }
+    return cudaErrorInvalidValue;
+  }
   for (int it = 0; it <= max_refine; ++it) {
     switch (m->nb) {
-#define X(n)                                                  \
-  case n:                                                     \
-    launch_iteration<n>(*m, r, x, it, max_refine, tol, st);   \
+#define X(n)                                                     \
+  case n:                                                        \
+    launch_iteration<n>(*m, r, x, it, max_refine, tol, st, 0, true); \
     break;
       BM_TAIL_NB_LIST(X)
 #undef X
     }
   }
+  return cudaPeekAtLastError();
 }
 
-int mixed_launches_per_solve(int max_refine) { return 3 * (max_refine + 1); }
 
 void mixed_launch_export(MixedState *m, double *Ld, double *Ll, double *Lr, double *F, double *LR,
                          cudaStream_t st) {

@@ -10,7 +10,7 @@ struct IRCtl {
   int converged;            // stop flag: the stopping test held, or refinement stalled
   int iters;                // corrections applied in the last solve
   unsigned wmax;            // max_i omega_i of the running iteration (bits of a non-negative float)
-  int pad;
+  int loop;                 // index of the next iteration (read by the kernels of a graph loop body)
   double omega_prev;        // omega after the previous iteration
   double eta;               // omega after the last iteration
 };
@@ -71,6 +71,12 @@ struct MCfg {
 
 __device__ __forceinline__ bool ir_done(const IRCtl *ctl) {
   return *((volatile const int *)&ctl->converged) != 0;
+}
+
+// The iteration a kernel runs: its launch argument, or (iter < 0, inside the
+// body of a graph loop) the counter the previous iteration's stopping test left.
+__device__ __forceinline__ int ir_iter(const IRCtl *ctl, int iter) {
+  return iter >= 0 ? iter : *((volatile const int *)&ctl->loop);
 }
 
 // z - sum_k L[k] y[k] over one row of a tail block (row-major, contiguous)
@@ -160,6 +166,11 @@ __device__ __forceinline__ void fwd_tail(const MixedState &m, const double *__re
       }
       const bool elim = lastlvl || (q < N && ctz32(q) == lvl);
       const size_t zoff = (sb + (N - q)) * NB;
+      // row i of L_qq and 1/L_ii first, so that they share the gather's
+      // memory round trip (in bounds for every q)
+      float Lrow[NB];
+      load_row<NB>(Lrow, m.Ld + (sb + (N - q)) * NB2 + (i < NB ? i : 0) * NB);
+      const float inv = i < NB ? m.invd[zoff + i] : 0.0f;
       float z = 0.0f;
       if (i < NB) {
         z = (lvl <= 1) ? d2f_rn(rhs[zoff + i]) : __ldcg(m.zt + zoff + i);
@@ -181,9 +192,6 @@ __device__ __forceinline__ void fwd_tail(const MixedState &m, const double *__re
         if (i < NB) m.zt[zoff + i] = z;
         continue;
       }
-      float Lrow[NB];
-      load_row<NB>(Lrow, m.Ld + (sb + (N - q)) * NB2 + (i < NB ? i : 0) * NB);
-      const float inv = i < NB ? m.invd[zoff + i] : 0.0f;
       if (TS <= 32) {
         const int base = (threadIdx.x & 31) & ~(TS - 1);
 #pragma unroll
@@ -293,6 +301,12 @@ __device__ __forceinline__ void bwd_tail(const MixedState &m, double *x, int ite
     for (int t = crank * TEAMS + tm.id; t < ntask; t += CS * TEAMS) {
       const int q = first ? N : (2 * t + 1) << lvl;
       const size_t zoff = (sb + (N - q)) * NB;
+      // column i of L_qq and 1/L_ii, loaded with the gather's operands
+      float Lcol[NB];
+      const float *Ld = m.Ld + (sb + (N - q)) * NB2 + (i < NB ? i : 0);
+#pragma unroll
+      for (int k = 0; k < NB; ++k) Lcol[k] = Ld[k * NB];
+      const float inv = i < NB ? m.invd[zoff + i] : 0.0f;
       float z = 0.0f;
       if (i < NB) {
         if (first) {
@@ -308,11 +322,6 @@ __device__ __forceinline__ void bwd_tail(const MixedState &m, double *x, int ite
           if (q > h) z = col_dot_sub<NB>(m.Ll + (sb + (N - q)) * NB2 + i, m.y + (sb + (N - a)) * NB, z);
         }
       }
-      float Lcol[NB];
-      const float *Ld = m.Ld + (sb + (N - q)) * NB2 + (i < NB ? i : 0);
-#pragma unroll
-      for (int k = 0; k < NB; ++k) Lcol[k] = Ld[k * NB];
-      const float inv = i < NB ? m.invd[zoff + i] : 0.0f;
       if (TS <= 32) {
         const int base = (threadIdx.x & 31) & ~(TS - 1);
 #pragma unroll
@@ -486,8 +495,9 @@ __device__ __forceinline__ float residual_root_row(const MixedState &m, const do
 // The stopping test of one refinement iteration, by one thread once every
 // row's omega is in: converged when omega <= tol; BM_ERR_NOT_CONVERGED after
 // max_iter corrections, or earlier when omega fails to halve (stalled or
-// diverging refinement), which also stops the remaining launches.
-__device__ __forceinline__ void ir_stop(const MixedState &m, float root_omega, int iter, int max_iter, double tol) {
+// diverging refinement), which also stops the remaining launches. Returns
+// true when another iteration is to run.
+__device__ __forceinline__ bool ir_stop(const MixedState &m, float root_omega, int iter, int max_iter, double tol) {
   IRCtl *ctl = m.ctl;
   const unsigned wb = atomicAdd(&ctl->wmax, 0u);
   const float wf = fmaxf(__uint_as_float(wb), root_omega);
@@ -504,6 +514,8 @@ __device__ __forceinline__ void ir_stop(const MixedState &m, float root_omega, i
   }
   ctl->omega_prev = omega;
   ctl->wmax = 0u;
+  ctl->loop = iter + 1;
+  return ctl->converged == 0;
 }
 
 // Root rows and the stopping test of one system, by its last CTA.

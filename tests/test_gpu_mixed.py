@@ -148,6 +148,58 @@ def test_mixed_is_deterministic():
     solver.close()
 
 
+@pytest.mark.parametrize("tol,max_refine", [(1e-10, 10), (1e-14, 10), (1e-30, 3), (1e-30, 1), (1e-30, 0)])
+def test_mixed_graph_loop_and_direct_launch_agree_bitwise(tol, max_refine):
+    """The captured solve (refinement as a conditional loop node) and the
+    directly launched, unrolled solve give the same bits, iteration count,
+    status and backward error: on convergence, on reaching max_refine and
+    on a stall."""
+    bm = _bm()
+    S, N, nb, nr = 3, 21, 8, 3
+    d = gen(S, N, nb, nr, seed=12, barrier=(-3, 3))
+    g = to_dev(d)
+    outs = []
+    for flags in (0, bm.BM_FLAG_NO_GRAPH):
+        solver = bm.BranchKKTSolver(S, N, nb, nr, precision=bm.BM_PREC_FP32_IR, max_refine=max_refine, tol=tol,
+                                    flags=flags)
+        solver.factor(g["D"], g["E"], g["C"], g["R"])
+        x = solver.solve(g["r"])
+        outs.append((x.cpu().numpy(), solver.query()))
+        solver.close()
+    (xa, ia), (xb, ib) = outs
+    assert np.array_equal(xa, xb)
+    for k in ("status", "iters", "backward_error"):
+        assert ia[k] == ib[k], (k, ia, ib)
+    assert ia["iters"] <= (max_refine if max_refine > 0 else 10)   # <= 0 selects the default, 10
+    if tol == 1e-30:
+        assert ia["status"] == 5, ia
+
+
+def test_mixed_graph_loop_restarts_on_replay():
+    """A replay of the captured solve runs the whole loop again: with the
+    right-hand side scaled by -2 in place (same pointers, so the same graph),
+    every step of the method scales exactly, so the solution must be exactly
+    -2 times the first one after the same number of corrections."""
+    bm = _bm()
+    S, N, nb, nr = 2, 17, 6, 3
+    d = gen(S, N, nb, nr, seed=4, barrier=(-3, 3))
+    g = to_dev(d)
+    solver = bm.BranchKKTSolver(S, N, nb, nr, precision=bm.BM_PREC_FP32_IR, tol=1e-13)
+    solver.factor(g["D"], g["E"], g["C"], g["R"])
+    r = g["r"].clone()
+    x = torch.empty_like(r)
+    solver.solve(r, x)
+    i1 = solver.query()
+    x1 = x.clone()
+    r.mul_(-2.0)
+    solver.solve(r, x)
+    i2 = solver.query()
+    solver.close()
+    assert i1["status"] == 0 and i2["status"] == 0 and i1["iters"] >= 1
+    assert i2["iters"] == i1["iters"]
+    assert torch.equal(x, -2.0 * x1)
+
+
 def test_mixed_not_spd_is_reported():
     bm = _bm()
     d = gen(2, 8, 4, 2, seed=6)
