@@ -166,11 +166,16 @@ __device__ __forceinline__ void fwd_tail(const MixedState &m, const double *__re
       }
       const bool elim = lastlvl || (q < N && ctz32(q) == lvl);
       const size_t zoff = (sb + (N - q)) * NB;
-      // row i of L_qq and 1/L_ii first, so that they share the gather's
-      // memory round trip (in bounds for every q)
+      // row i of L_qq and 1/L_ii: for NB <= 16 loaded first, so that they
+      // share the gather's memory round trip (in bounds for every q); for
+      // larger blocks after it (loaded first they slowed the nb = 48 solve)
+      constexpr bool kEarly = NB <= 16;
       float Lrow[NB];
-      load_row<NB>(Lrow, m.Ld + (sb + (N - q)) * NB2 + (i < NB ? i : 0) * NB);
-      const float inv = i < NB ? m.invd[zoff + i] : 0.0f;
+      float inv = 0.0f;
+      if constexpr (kEarly) {
+        load_row<NB>(Lrow, m.Ld + (sb + (N - q)) * NB2 + (i < NB ? i : 0) * NB);
+        inv = i < NB ? m.invd[zoff + i] : 0.0f;
+      }
       float z = 0.0f;
       if (i < NB) {
         z = (lvl <= 1) ? d2f_rn(rhs[zoff + i]) : __ldcg(m.zt + zoff + i);
@@ -191,6 +196,10 @@ __device__ __forceinline__ void fwd_tail(const MixedState &m, const double *__re
       if (!elim) {
         if (i < NB) m.zt[zoff + i] = z;
         continue;
+      }
+      if constexpr (!kEarly) {
+        load_row<NB>(Lrow, m.Ld + (sb + (N - q)) * NB2 + (i < NB ? i : 0) * NB);
+        inv = i < NB ? m.invd[zoff + i] : 0.0f;
       }
       if (TS <= 32) {
         const int base = (threadIdx.x & 31) & ~(TS - 1);
@@ -301,12 +310,17 @@ __device__ __forceinline__ void bwd_tail(const MixedState &m, double *x, int ite
     for (int t = crank * TEAMS + tm.id; t < ntask; t += CS * TEAMS) {
       const int q = first ? N : (2 * t + 1) << lvl;
       const size_t zoff = (sb + (N - q)) * NB;
-      // column i of L_qq and 1/L_ii, loaded with the gather's operands
+      // column i of L_qq and 1/L_ii: loaded with the gather's operands for
+      // NB <= 16, after the gather for larger blocks
+      constexpr bool kEarly = NB <= 16;
       float Lcol[NB];
-      const float *Ld = m.Ld + (sb + (N - q)) * NB2 + (i < NB ? i : 0);
+      float inv = 0.0f;
+      if constexpr (kEarly) {
+        const float *Ld = m.Ld + (sb + (N - q)) * NB2 + (i < NB ? i : 0);
 #pragma unroll
-      for (int k = 0; k < NB; ++k) Lcol[k] = Ld[k * NB];
-      const float inv = i < NB ? m.invd[zoff + i] : 0.0f;
+        for (int k = 0; k < NB; ++k) Lcol[k] = Ld[k * NB];
+        inv = i < NB ? m.invd[zoff + i] : 0.0f;
+      }
       float z = 0.0f;
       if (i < NB) {
         if (first) {
@@ -321,6 +335,12 @@ __device__ __forceinline__ void bwd_tail(const MixedState &m, double *x, int ite
           z = col_dot_sub<NB>(m.Lr + (sb + (N - q)) * NB2 + i, m.y + (sb + (N - b)) * NB, z);
           if (q > h) z = col_dot_sub<NB>(m.Ll + (sb + (N - q)) * NB2 + i, m.y + (sb + (N - a)) * NB, z);
         }
+      }
+      if constexpr (!kEarly) {
+        const float *Ld = m.Ld + (sb + (N - q)) * NB2 + (i < NB ? i : 0);
+#pragma unroll
+        for (int k = 0; k < NB; ++k) Lcol[k] = Ld[k * NB];
+        inv = i < NB ? m.invd[zoff + i] : 0.0f;
       }
       if (TS <= 32) {
         const int base = (threadIdx.x & 31) & ~(TS - 1);
