@@ -199,6 +199,47 @@ def bm_status_string(code: int) -> str:
     return _load().bm_status_string(int(code)).decode()
 
 
+# block sizes with compiled tail kernels (factor and cluster solve)
+TAIL_NB = (2, 3, 4, 6, 8, 12, 16, 24, 32, 48)
+
+
+def chain_levels(N: int) -> int:
+    """Odd-even levels of the N - 1 chain positions of a tail (Sec. II)."""
+    return (N - 1).bit_length() if N > 1 else 0
+
+
+def top_level(N: int) -> int:
+    """First level with at most four positions per tail: it and the levels
+    above it run in one launch per tail."""
+    for lvl in range(chain_levels(N)):
+        if (N // 2 if lvl == 0 else ((N - 1) >> lvl) + 1) <= 4:
+            return lvl
+    return chain_levels(N)
+
+
+def launches_per_step(S, N, nb, nr, precision=BM_PREC_FP64, max_refine=10, iters=None) -> int:
+    """Kernels that one bm_factor + one bm_solve launch.
+
+    Factor: one launch per level below ``top_level(N)``, one for the top
+    levels and x_1, one for the root (with the per-level generic kernels,
+    used for block sizes without compiled tail kernels: one per level, one
+    for x_1, one for the root). FP64 solve: tail forward, root, tail
+    backward (generic kernels: one per level each way, plus x_1 forward,
+    root and x_1 backward). Mixed solve: three kernels per refinement
+    iteration; pass the corrections of the solve (``query()["iters"]``) for
+    a captured graph, whose loop stops after the last iteration that runs;
+    without it the count is the unrolled direct-launch bound
+    (``max_refine <= 0`` selects 10)."""
+    Lc = chain_levels(N)
+    if precision == BM_PREC_FP32_IR:
+        mr = max_refine if max_refine > 0 else 10
+        runs = mr + 1 if iters is None else min(int(iters), mr) + 1
+        return (top_level(N) + 2) + 3 * runs
+    if nb not in TAIL_NB:
+        return (Lc + 2) + (2 * Lc + 3)
+    return (top_level(N) + 2) + 3
+
+
 def make_desc(S, N, nb, nr, precision=BM_PREC_FP64, max_refine=10, tol=1e-10, flags=0) -> bm_desc:
     return bm_desc(int(S), int(N), int(nb), int(nr), int(precision), int(max_refine), float(tol), int(flags))
 
@@ -286,30 +327,10 @@ class BranchKKTSolver:
         return x
 
     def launches_per_step(self, iters=None) -> int:
-        """Kernels one bm_factor + one bm_solve launch. On the mixed path the
-        solve launches three kernels per refinement iteration: pass the
-        corrections of the solve (``query()["iters"]``) for the count of a
-        captured graph, whose loop stops after the last iteration that runs;
-        without it the count is the unrolled direct-launch bound."""
+        """Kernels one bm_factor + one bm_solve of this handle launch (see
+        the module-level ``launches_per_step``)."""
         S, N, nb, nr = self.shape
-        if self.desc.precision == BM_PREC_FP32_IR:
-            Lc = (N - 1).bit_length() if N > 1 else 0
-            top = Lc
-            for lvl in range(Lc):
-                if (N // 2 if lvl == 0 else ((N - 1) >> lvl) + 1) <= 4:
-                    top = lvl
-                    break
-            runs = self.desc.max_refine + 1 if iters is None else min(int(iters), self.desc.max_refine) + 1
-            return (top + 2) + 3 * runs
-        Lc = (N - 1).bit_length() if N > 1 else 0
-        if nb not in (2, 3, 4, 6, 8, 12, 16, 24, 32, 48):
-            return (Lc + 2) + (2 * Lc + 3)
-        top = Lc
-        for lvl in range(Lc):   # first level with at most four positions per tail
-            if (N // 2 if lvl == 0 else ((N - 1) >> lvl) + 1) <= 4:
-                top = lvl
-                break
-        return (top + 2) + 3
+        return launches_per_step(S, N, nb, nr, self.desc.precision, self.desc.max_refine, iters)
 
     def query(self, stream=None) -> dict:
         return bm_query(self.h, stream)

@@ -1,0 +1,36 @@
+"""The kernel counts the bench reports (``gpu_launches``), checked on CPU
+against counts taken by hand from the launch sequence of the library:
+factor = one launch per level below the top level, one top launch, one
+root launch; FP64 solve = forward, root, backward; mixed solve = three
+kernels per refinement iteration."""
+from paper_2609_29977_gb300 import bm as core
+
+
+def test_levels_of_the_medium_workload():
+    # N = 64: 63 chain positions, levels 0..5 (+ x_1); per-tail positions by
+    # level 32, 32, 16, 8, 4 -> level 4 is the first with at most four
+    assert core.chain_levels(64) == 6
+    assert core.top_level(64) == 4
+    assert core.chain_levels(1) == 0 and core.top_level(1) == 0
+    assert core.chain_levels(2) == 1 and core.top_level(2) == 0     # one chain position
+    assert core.top_level(9) == 0      # level 0 already has N/2 = 4 positions
+    assert core.top_level(10) == 2     # levels 0, 1, 2: 5, 5, 3 positions (level 1 holds 4 eliminations + x_1's update)
+
+
+def test_fp64_counts():
+    # medium: 4 level launches + top + root, then forward + root + backward
+    assert core.launches_per_step(64, 64, 12, 4) == 9
+    # a block size without compiled tail kernels (generic per-level path)
+    Lc = core.chain_levels(9)
+    assert Lc == 4
+    assert core.launches_per_step(2, 9, 5, 3) == (Lc + 2) + (2 * Lc + 3) == 17
+
+
+def test_mixed_counts():
+    # medium, 2 corrections in a captured graph: 6 factor + 3 x 3 solve
+    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2) == 15
+    # directly launched: all 11 iterations
+    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10) == 6 + 33
+    # max_refine <= 0 selects 10; the count never exceeds max_refine + 1 iterations
+    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 0) == 6 + 33
+    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 3, iters=7) == 6 + 12
