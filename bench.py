@@ -67,14 +67,10 @@ def fp32_peak_gflops(sm_mhz=None):
 
 def _factor_kernels(N, nb, precision):
     """Names of the kernels one factor launches (one CUDA graph)."""
-    Lc = (N - 1).bit_length() if N > 1 else 0
-    top = Lc
-    for lvl in range(Lc):
-        if (N // 2 if lvl == 0 else ((N - 1) >> lvl) + 1) <= 4:
-            top = lvl
-            break
+    from paper_2609_29977_gb300 import bm as core   # plain Python: does not load the library
+    Lc, top = core.chain_levels(N), core.top_level(N)
     if precision == "fp64":
-        if nb in (2, 3, 4, 6, 8, 12, 16, 24, 32, 48):
+        if nb in core.TAIL_NB:
             return "k_factor_level_team x%d + k_factor_top + k_factor_root" % top
         return "k_factor_level x%d + k_factor_x1 + k_factor_root" % Lc
     suffix = "" if nb <= 32 else "_w"
