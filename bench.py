@@ -1,14 +1,21 @@
 """Benchmark: factor + solve of one branch-MPC KKT system per step.
 
-Default workload: the medium FP64 system (S=64 scenarios, N=64 stages,
-nb=12, nr=4, barrier diagonals 10^U[-4,4]), factored (Alg. 1) and solved
-(Alg. 2) through the C ABI with the inputs resident in HBM. One step =
-bm_factor + bm_solve. L2 is flushed (a 256 MiB write) between timed steps,
-outside the timed events.
+Default workload: the mixed-precision system of the headline metric (S=512
+scenarios, N=128 stages, nb=24, nr=8, barrier diagonals 10^U[-6,6]),
+factored (Alg. 1) and solved (Alg. 2) through the C ABI with the inputs
+resident in HBM (605 MB of FP64 blocks, larger than L2; L2 is also flushed
+by a 256 MiB write between timed steps, outside the timed events). One step
+= bm_factor + bm_solve.
 
-Prints ONE JSON line (rank 0). value = whole-job GFLOP/s, counting the
-method's flops of one factor + solve per step (the same per-step count for
-every arm, so value is proportional to KKT systems per second).
+Prints ONE JSON line (rank 0). value = whole-job GFLOP/s of the plain FP64
+path, counting the method's flops of one factor + solve per step (the same
+per-step count for every arm, so value is proportional to KKT systems per
+second). Beside it, on the same system: "fp32ir_same_workload" (FP32 tails +
+FP64 refinement to omega <= 1e-10, with its status, backward errors and
+forward error against the FP64 solution) and, for the default workload on
+one GPU, "batched" (256 uneven systems in one persistent launch against the
+FP64 path one system at a time) and "serving" (the Poisson request stream,
+FP32+IR against FP64, p50/p99 latency); --no-forms skips those two.
   --impl reference : the CPU oracle (natural-order FP64 block Cholesky) on
                      the host cores, timed on the same workload.
   --workload NAME  : another synthetic workload (see bmgen.WORKLOADS).
@@ -30,7 +37,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-DEFAULT_WORKLOAD = "medium-s64-n64-nb12"
+DEFAULT_WORKLOAD = "mixed-s512-n128-nb24"
 METRIC = "factor+solve µs and GFLOP/s per branch KKT; FP32+IR vs FP64 at rel. residual 1e-10"
 L2_FLUSH_BYTES = 256 << 20
 
@@ -276,6 +283,11 @@ def run_reference(args):
 
 
 def run_batched(args):
+    print(json.dumps(batched_line(args, args.steps, args.warmup)), flush=True)
+    return 0
+
+
+def batched_line(args, steps, warmup):
     """The batched workload: 256 systems with S~U{8..256}, N~U{16..256},
     nb in {6,12,24,48}, nr = ceil(nb/3), barrier 10^U[-4,4], factored in one
     persistent launch and solved with FP32 tails + FP64 refinement. One step
@@ -305,19 +317,19 @@ def run_batched(args):
     batch.factor(Ds, Es, Cs, Rs)     # first call autotunes the persistent launch
     torch.cuda.synchronize()
     tune_s = time.perf_counter() - t0
-    for _ in range(max(3, args.warmup)):
+    for _ in range(max(3, warmup)):
         batch.factor(Ds, Es, Cs, Rs)
         batch.solve(rs, xs)
     infos = batch.query()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+           torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     sampler = ClockSampler("0")
     sampler.start()
     time.sleep(0.5)
     torch.cuda.synchronize()
-    for i in range(args.steps):
+    for i in range(steps):
         flush.zero_()
         a, b, c = ev[i]
         a.record(stream)
@@ -360,8 +372,8 @@ def run_batched(args):
             del x64
     ms = fac + sol
     line = {
-        "metric": METRIC, "value": flops / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": flops / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "n_gpus": 1, "steps": steps,
+        "warmup": max(3, warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (seeded MPC-shaped generator)",
         "config": {"workload": "batched-%d" % count, "systems": count, "stages": sum(S * N for S, N, _, _ in shapes),
                    "precision": "fp32ir", "tol": args.tol, "l2": "flushed between timed steps"},
@@ -371,8 +383,9 @@ def run_batched(args):
         "forward_error_vs_fp64_max": fwd_max if fp64_ms is not None else None,
         "autotune_s": tune_s, "generate_s": gen_s, "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
-    return 0
+    del systems, Ds, Es, Cs, Rs, rs, xs
+    torch.cuda.empty_cache()
+    return line
 
 
 def _percentile(vals, q):
@@ -386,6 +399,11 @@ def _percentile(vals, q):
 
 
 def run_serving(args):
+    print(json.dumps(serving_line(args)), flush=True)
+    return 0
+
+
+def serving_line(args):
     """Serving: a Poisson stream of requests (mean --rate per second), each a
     branch-MPC system drawn as in the batched workload (S~U{8..256},
     N~U{16..256}, nb in {6,12,24,48}, nr = ceil(nb/3)) or, with probability
@@ -520,8 +538,9 @@ def run_serving(args):
         "throughput_vs_fp64": main["throughput_req_s"] / runs["fp64"]["throughput_req_s"],
         "generate_s": gen_s,
     }
-    print(json.dumps(line), flush=True)
-    return 0
+    del pool, xs
+    torch.cuda.empty_cache()
+    return line
 
 
 def run_assembly(args):
@@ -859,24 +878,39 @@ def run_gpu(args):
             mixed.factor(g["D"], g["E"], g["C"], g["R"])
             mixed.solve(g["r"], xm)
         k = min(args.steps, 1000)
-        evm = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        evm = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+                torch.cuda.Event(enable_timing=True)) for _ in range(k)]
         torch.cuda.synchronize()
-        for a, b in evm:
+        for a, b, c in evm:
             flush.zero_()
             a.record(stream)
             mixed.factor(g["D"], g["E"], g["C"], g["R"])
-            mixed.solve(g["r"], xm)
             b.record(stream)
+            mixed.solve(g["r"], xm)
+            c.record(stream)
         torch.cuda.synchronize()
-        mms = statistics.mean(a.elapsed_time(b) for a, b in evm)
+        mfac = statistics.mean(a.elapsed_time(b) for a, b, _ in evm)
+        msol = statistics.mean(b.elapsed_time(c) for _, b, c in evm)
+        mms = mfac + msol
         minfo = mixed.query()
         mmeas = gpu_residual_measures(g, xm)
         line["fp32ir_same_workload"] = {
-            "us_per_kkt": mms * 1e3, "value": world * fl["total"] / (mms * 1e-3) / 1e9, "unit": "GFLOP/s",
+            "us_per_kkt": mms * 1e3, "factor_us": mfac * 1e3, "solve_us": msol * 1e3,
+            "value": world * fl["total"] / (mms * 1e-3) / 1e9, "unit": "GFLOP/s",
             "steps": k, **mmeas, "refinement_steps": minfo["iters"],
+            "coupling_refined": minfo["coupling_refined"],
             "forward_error_vs_fp64": float((xm - x).abs().max() / x.abs().max()),
-            "device_status": minfo["name"], "speedup_vs_fp64": ms_per_step / mms}
+            "device_status": minfo["name"], "speedup_vs_fp64": ms_per_step / mms,
+            "gpu_launches_per_step": mixed.launches_per_step(minfo.get("iters"))}
         mixed.close()
+        del xm
+    if world == 1 and rank == 0 and not args.no_forms and w.name == DEFAULT_WORKLOAD and not args.shape:
+        # the batched and serving forms of the method on their own workloads,
+        # reported beside the single-system line (each its own timed region)
+        del g, x
+        torch.cuda.empty_cache()
+        line["batched"] = _sub_line(lambda: _batched_summary(batched_line(args, min(args.steps, 3), 2)))
+        line["serving"] = _sub_line(lambda: _serving_summary(serving_line(args)))
     if dist:
         dist.destroy_process_group()
     if rank == 0:
@@ -884,10 +918,35 @@ def run_gpu(args):
     return 0
 
 
+def _sub_line(fn):
+    try:
+        return fn()
+    except Exception as e:   # a failing form is reported, not fatal to the main line
+        return {"error": "%s: %s" % (type(e).__name__, e)}
+
+
+def _batched_summary(b):
+    keep = ("value", "unit", "ms_per_step", "factor_ms", "solve_ms", "fp64_sequential_ms",
+            "speedup_vs_fp64_sequential", "omega_max", "failed_systems", "forward_error_vs_fp64_max",
+            "schedule", "steps", "warmup", "clocks")
+    out = {k: b.get(k) for k in keep}
+    out["config"] = b.get("config")
+    return out
+
+
+def _serving_summary(sv):
+    out = {k: sv.get(k) for k in ("value", "unit", "p50_ms", "p99_ms", "throughput_vs_fp64", "config")}
+    out["runs"] = {name: {k: r.get(k) for k in ("offered_rate", "throughput_req_s", "gflops", "p50_ms", "p99_ms",
+                                                 "failed", "fp64_fallbacks", "device_omega_max",
+                                                 "sample_omega_max")}
+                   for name, r in sv.get("runs", {}).items()}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
@@ -912,6 +971,8 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=160.0, help="serving: HBM arena")
     ap.add_argument("--seed", type=int, default=2000)
     ap.add_argument("--gen-device", default="cuda", help="batched: where the systems are drawn (cuda or cpu)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="default workload: skip the batched and serving sub-runs reported beside the main line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -67,6 +67,19 @@ typedef enum {
 
 /* bm_desc.flags */
 #define BM_FLAG_NO_GRAPH 1u /* launch kernels directly instead of replaying captured CUDA graphs */
+/*
+ * BM_PREC_FP32_IR only: how the root Schur complement R~ = R - sum_i U_i is
+ * formed (Alg. 1 steps 3-4). By default (neither flag) the factor first
+ * forms it from the FP32 tail factor; when that Cholesky fails, or some
+ * diagonal entry cancels by more than 2^12 (R_jj > 4096 R~_jj), it refines
+ * each tail's coupling columns X_i = K_i^{-1} C_i^T (the nr columns through
+ * which the tail meets the root) with the FP32 factor and one FP64-accurate
+ * residual, forms U_i = C_{i,1} X_i from them, refactors the root, and the
+ * solves then use X_i for the root coupling. The flags force one choice.
+ * Setting both is BM_ERR_INVALID_ARG.
+ */
+#define BM_FLAG_COUPLING_REFINE 2u /* always refine the coupling columns */
+#define BM_FLAG_COUPLING_FP32 4u   /* never: R~ from the FP32 tail factor alone */
 
 typedef struct {
   int S, N, nb, nr;   /* scenarios (the paper's M), horizon, stage block, root block */
@@ -82,6 +95,7 @@ typedef struct {
   int fail_stage;      /* BM_ERR_NOT_SPD: 1-based stage k of that tail, 0 for the root */
   int iters;           /* BM_PREC_FP32_IR: refinement steps of the last solve */
   double backward_error; /* BM_PREC_FP32_IR: componentwise backward error of the returned x; FP64: -1 */
+  int coupling_refined;  /* BM_PREC_FP32_IR: 1 if the last bm_factor refined the coupling columns */
 } bm_info;
 
 /* Library version (BM_VERSION). */

@@ -16,6 +16,8 @@ _LIB_PATH = os.path.join(HERE, "libbm.so")
 BM_PREC_FP64 = 0
 BM_PREC_FP32_IR = 1
 BM_FLAG_NO_GRAPH = 1
+BM_FLAG_COUPLING_REFINE = 2   # mixed precision: always refine the coupling columns
+BM_FLAG_COUPLING_FP32 = 4     # mixed precision: never (root from the FP32 tail factor alone)
 
 BM_OK = 0
 STATUS_NAMES = {0: "BM_OK", 1: "BM_ERR_INVALID_ARG", 2: "BM_ERR_NOT_SPD", 3: "BM_ERR_OOM",
@@ -45,7 +47,7 @@ class bm_desc(ctypes.Structure):
 
 class bm_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("fail_scenario", ctypes.c_int), ("fail_stage", ctypes.c_int),
-                ("iters", ctypes.c_int), ("backward_error", ctypes.c_double)]
+                ("iters", ctypes.c_int), ("backward_error", ctypes.c_double), ("coupling_refined", ctypes.c_int)]
 
 
 class bm_qp_desc(ctypes.Structure):
@@ -217,7 +219,7 @@ def top_level(N: int) -> int:
     return chain_levels(N)
 
 
-def launches_per_step(S, N, nb, nr, precision=BM_PREC_FP64, max_refine=10, iters=None) -> int:
+def launches_per_step(S, N, nb, nr, precision=BM_PREC_FP64, max_refine=10, iters=None, flags=0) -> int:
     """Kernels that one bm_factor + one bm_solve launch.
 
     Factor: one launch per level below ``top_level(N)``, one for the top
@@ -225,16 +227,26 @@ def launches_per_step(S, N, nb, nr, precision=BM_PREC_FP64, max_refine=10, iters
     used for block sizes without compiled tail kernels: one per level, one
     for x_1, one for the root). FP64 solve: tail forward, root, tail
     backward (generic kernels: one per level each way, plus x_1 forward,
-    root and x_1 backward). Mixed solve: three kernels per refinement
-    iteration; pass the corrections of the solve (``query()["iters"]``) for
-    a captured graph, whose loop stops after the last iteration that runs;
-    without it the count is the unrolled direct-launch bound
-    (``max_refine <= 0`` selects 10)."""
+    root and x_1 backward). Mixed factor: the tail launches, then with
+    BM_FLAG_COUPLING_FP32 the root; with BM_FLAG_COUPLING_REFINE the four
+    coupling-column launches and the root; by default the probing root, the
+    four coupling-column launches and a second root (the last five return at
+    once when the probe does not engage the refinement). Mixed solve: three
+    kernels per refinement iteration; pass the corrections of the solve
+    (``query()["iters"]``) for a captured graph, whose loop stops after the
+    last iteration that runs; without it the count is the unrolled
+    direct-launch bound (``max_refine <= 0`` selects 10)."""
     Lc = chain_levels(N)
     if precision == BM_PREC_FP32_IR:
         mr = max_refine if max_refine > 0 else 10
         runs = mr + 1 if iters is None else min(int(iters), mr) + 1
-        return (top_level(N) + 2) + 3 * runs
+        if flags & BM_FLAG_COUPLING_FP32:
+            factor = top_level(N) + 2
+        elif flags & BM_FLAG_COUPLING_REFINE:
+            factor = top_level(N) + 6
+        else:
+            factor = top_level(N) + 7
+        return factor + 3 * runs
     if nb not in TAIL_NB:
         return (Lc + 2) + (2 * Lc + 3)
     return (top_level(N) + 2) + 3
@@ -268,7 +280,7 @@ def bm_query(h, stream=None) -> dict:
     code = _load().bm_query(h, _stream(stream), ctypes.byref(info))
     return {"status": int(code), "name": STATUS_NAMES.get(int(code), str(code)),
             "fail_scenario": info.fail_scenario, "fail_stage": info.fail_stage, "iters": info.iters,
-            "backward_error": info.backward_error}
+            "backward_error": info.backward_error, "coupling_refined": int(info.coupling_refined)}
 
 
 def bm_export_factor(h, Ld=None, Ll=None, Lr=None, F=None, LR=None, stream=None) -> None:
@@ -330,7 +342,7 @@ class BranchKKTSolver:
         """Kernels one bm_factor + one bm_solve of this handle launch (see
         the module-level ``launches_per_step``)."""
         S, N, nb, nr = self.shape
-        return launches_per_step(S, N, nb, nr, self.desc.precision, self.desc.max_refine, iters)
+        return launches_per_step(S, N, nb, nr, self.desc.precision, self.desc.max_refine, iters, self.desc.flags)
 
     def query(self, stream=None) -> dict:
         return bm_query(self.h, stream)

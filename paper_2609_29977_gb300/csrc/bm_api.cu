@@ -20,9 +20,9 @@ void f64_launch_solve(const F64View &v, const double *r, double *x, double *r0t,
 
 // mixed precision path (bm_mixed.cu)
 struct MixedState;
-size_t mixed_bytes(int S, int N, int nb, int nr);
+size_t mixed_bytes(int S, int N, int nb, int nr, int cmode);
 cudaError_t mixed_prepare(int nb, int nr);
-MixedState *mixed_create(int S, int N, int nb, int nr, void *base, size_t bytes, Status *status,
+MixedState *mixed_create(int S, int N, int nb, int nr, int cmode, void *base, size_t bytes, Status *status,
                          unsigned *tickets, cudaStream_t init_stream, bool sync_init);
 void mixed_destroy(MixedState *m);
 void mixed_launch_factor(MixedState *m, const double *D, const double *E, const double *C,
@@ -70,7 +70,16 @@ static bool valid_desc(const bm_desc *d) {
   if (d->nb > 64 || d->nr > 64 || d->S > 65535) return false;
   if (d->N > (1 << 24)) return false;
   if (d->precision != BM_PREC_FP64 && d->precision != BM_PREC_FP32_IR) return false;
+  if ((d->flags & BM_FLAG_COUPLING_REFINE) && (d->flags & BM_FLAG_COUPLING_FP32)) return false;
   return true;
+}
+
+// Coupling-column mode of the mixed path: 0 = FP32-based root, 1 = automatic,
+// 2 = always refine.
+static int coupling_mode(const bm_desc *d) {
+  if (d->flags & BM_FLAG_COUPLING_FP32) return 0;
+  if (d->flags & BM_FLAG_COUPLING_REFINE) return 2;
+  return 1;
 }
 
 static size_t f64_bytes(int S, int N, int nb, int nr) {
@@ -110,7 +119,7 @@ extern "C" size_t bm_workspace_bytes(const bm_desc *d) {
   if (d->precision == BM_PREC_FP64)
     t += f64_bytes(d->S, d->N, d->nb, d->nr);
   else
-    t += mixed_bytes(d->S, d->N, d->nb, d->nr);
+    t += mixed_bytes(d->S, d->N, d->nb, d->nr, coupling_mode(d));
   return t;
 }
 
@@ -171,7 +180,7 @@ bm_status analyze_impl(const bm_desc *desc, void *mem, size_t bytes, cudaStream_
     if (f64_prepare(nb, nr) != cudaSuccess) goto cuda_fail;
   } else {
     if (mixed_prepare(nb, nr) != cudaSuccess) goto cuda_fail;
-    h->mixed = mixed_create(S, N, nb, nr, (char *)h->pool + kHeader, h->pool_bytes - kHeader, h->status,
+    h->mixed = mixed_create(S, N, nb, nr, coupling_mode(desc), (char *)h->pool + kHeader, h->pool_bytes - kHeader, h->status,
                             h->tickets, light ? init_stream : nullptr, !light);
     if (!h->mixed) goto cuda_fail;
   }
@@ -347,6 +356,7 @@ extern "C" bm_status bm_query(bm_handle h, void *stream, bm_info *info) {
     info->fail_stage = st.code == BM_ERR_NOT_SPD ? st.stage : 0;
     info->iters = h->mixed ? st.iters : 0;
     info->backward_error = h->mixed ? st.eta : -1.0;
+    info->coupling_refined = h->mixed ? st.coupled : 0;
   }
   return (bm_status)st.code;
 }

@@ -103,7 +103,7 @@ __device__ void root_item(const BInst &I, const double *R, int lane, int TS, uns
   for (int e = lane; e < nr * nr; e += TS) {
     const int i = e / nr, j = e - i * nr;
     if (j > i) continue;
-    const double v = R[i * nr + j] - root_sum(U, S, nr, i, j);
+    const double v = R[i * nr + j] - root_sum_serial(U, S, nr, i, j);
     Rt[i * nr + j] = v;
     Rt[j * nr + i] = v;
     LR[i * nr + j] = v;
@@ -752,6 +752,7 @@ extern "C" bm_status bm_batch_query(bm_batch h, void *stream, bm_info *infos) {
       infos[b].fail_stage = st[b].code == BM_ERR_NOT_SPD ? st[b].stage : 0;
       infos[b].iters = st[b].iters;
       infos[b].backward_error = st[b].eta;
+      infos[b].coupling_refined = 0;
     }
     if (first == BM_OK && st[b].code != 0) first = (bm_status)st[b].code;
   }

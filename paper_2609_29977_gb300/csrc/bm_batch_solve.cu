@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(256) k_batch_fwd(const BInst *inst, const BTai
 #define X(n)                                                              \
   case n:                                                                 \
     fwd_tail<n>(I.m, rhs, t.s, 0, 1, reinterpret_cast<float(*)[n]>(sbuf)); \
-    if (last_cta(&I.m.tickets[2], (unsigned)I.S)) root_step<n>(I.m, rhs, xp[t.inst], iter, sR); \
+    if (last_cta(&I.m.tickets[2], (unsigned)I.S)) root_step<n>(I.m, rhs, xp[t.inst], iter, sR, I.S); \
     break;
     BM_BATCH_NB_LIST(X)
 #undef X

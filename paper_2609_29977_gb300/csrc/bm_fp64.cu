@@ -26,6 +26,8 @@
 // single-lane FP64 work is the pivot reciprocal square root.
 #include <math.h>
 
+#include <mutex>
+
 #include "bm_internal.cuh"
 
 namespace bm {
@@ -249,20 +251,35 @@ __global__ void k_factor_x1(F64View v) {
   }
 }
 
-// Root: R~ = R - sum_i U_i (one thread per lower-triangle entry, fixed
-// summation order root_sum), then L_R = chol(R~) by the last CTA to finish
-// (Alg. 1, steps 4-5).
-__global__ void k_factor_root(F64View v) {
+// Cancellation above which the automatic mode of the mixed path refines the
+// coupling columns: R_jj / R~_jj > 2^12 for some j means that the FP32-based
+// R~ keeps fewer than about three of the digits its terms U_i carry.
+constexpr double kRootCancelEngage = 4096.0;
+
+// Root: R~ = R - sum_i U_i (one warp per lower-triangle entry, fixed
+// summation order root_sum_warp), then L_R = chol(R~) by the last CTA to
+// finish (Alg. 1, steps 4-5).
+//  mode 0: plain.
+//  mode 1: probe of the mixed path's automatic mode, with FP32-based U_i:
+//          when the Cholesky fails or the diagonal cancels by more than
+//          kRootCancelEngage, *on = 1 (the refinement of the coupling
+//          columns then runs and a mode-2 launch redoes the root) and no
+//          failure is reported; else *on = 0 and this is the final root.
+//  mode 2: the root after that refinement; returns at once unless *on.
+__global__ void __launch_bounds__(256) k_factor_root(F64View v, int mode, int *on) {
   extern __shared__ double sm[];
   __shared__ int sflag, last;
+  if (mode == 2 && *((volatile const int *)on) == 0) return;
   const int nr = v.nr, ne = nr * (nr + 1) / 2;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (e < ne) {
     int i, j;
     tri_ij(e, i, j);
-    const double val = v.R[i * nr + j] - root_sum(v.U, v.S, nr, i, j);
-    v.Rt[i * nr + j] = val;
-    v.Rt[j * nr + i] = val;
+    const double val = v.R[i * nr + j] - root_sum_warp(v.U, v.S, nr, i, j);
+    if ((threadIdx.x & 31) == 0) {
+      v.Rt[i * nr + j] = val;
+      v.Rt[j * nr + i] = val;
+    }
   }
   __threadfence();
   __syncthreads();
@@ -273,7 +290,20 @@ __global__ void k_factor_root(F64View v) {
   double *sR = sm, *sInv = sm + nr * nr;
   for (int k = threadIdx.x; k < nr * nr; k += blockDim.x) sR[k] = __ldcg(v.Rt + k);
   __syncthreads();
-  if (cta_chol(sR, sInv, nr, &sflag) && threadIdx.x == 0) report_not_spd(v.status, -1, 0);
+  bool engage = false;
+  if (mode == 1) {
+    for (int j = 0; j < nr; ++j) {
+      const double rt = sR[j * nr + j];
+      if (!(rt > 0.0) || v.R[j * nr + j] > kRootCancelEngage * rt) engage = true;
+    }
+  }
+  __syncthreads();
+  const int fail = cta_chol(sR, sInv, nr, &sflag);
+  if (mode == 1 && fail) engage = true;
+  if (threadIdx.x == 0) {
+    if (mode == 1) *on = engage ? 1 : 0;
+    if (fail && !engage) report_not_spd(v.status, -1, 0);
+  }
   cta_store_lower(v.LR, sR, nr);
   if (threadIdx.x == 0) v.tickets[0] = 0u;
 }
@@ -478,7 +508,9 @@ void f64_cluster_launch_solve(const F64View &v, const double *r, double *x, doub
 cudaError_t f64_prepare(int nb, int nr) {
   (void)nb;
   (void)nr;
+  static std::mutex mu;
   static bool done[64] = {false};
+  std::lock_guard<std::mutex> lock(mu);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorUnknown;
   if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
@@ -522,12 +554,13 @@ void f64_launch_factor(const F64View &v, cudaStream_t st) {
     k_factor_x1<<<v.S, T, smem, st>>>(v);
   }
   const int ne = v.nr * (v.nr + 1) / 2;
-  k_factor_root<<<(ne + 255) / 256, 256, ((size_t)v.nr * v.nr + v.nr) * sizeof(double), st>>>(v);
+  k_factor_root<<<(ne + 7) / 8, 256, ((size_t)v.nr * v.nr + v.nr) * sizeof(double), st>>>(v, 0, nullptr);
 }
 
-// Root step of the factor for callers that hold raw buffers (mixed path).
+// Root step of the factor for callers that hold raw buffers (mixed path);
+// mode and on as for k_factor_root.
 void f64_launch_factor_root_raw(int S, int nr, const double *U, const double *R, double *Rt, double *LR,
-                                unsigned *tickets, Status *status, cudaStream_t st) {
+                                unsigned *tickets, Status *status, int mode, int *on, cudaStream_t st) {
   F64View v{};
   v.S = S;
   v.nr = nr;
@@ -538,7 +571,7 @@ void f64_launch_factor_root_raw(int S, int nr, const double *U, const double *R,
   v.tickets = tickets;
   v.status = status;
   const int ne = nr * (nr + 1) / 2;
-  k_factor_root<<<(ne + 255) / 256, 256, ((size_t)nr * nr + nr) * sizeof(double), st>>>(v);
+  k_factor_root<<<(ne + 7) / 8, 256, ((size_t)nr * nr + nr) * sizeof(double), st>>>(v, mode, on);
 }
 
 void f64_launch_solve_root(const F64View &v, const double *r, double *x, double *r0t, cudaStream_t st) {

@@ -59,6 +59,8 @@ struct Status {
   int scenario;   // 0-based, -1 root
   int stage;      // 1-based natural stage, 0 root
   int iters;      // refinement steps
+  int coupled;    // mixed precision: the coupling columns were refined in the last factor
+  int pad_;
   double eta;     // refinement: componentwise backward error of the iterate
 };
 
@@ -70,28 +72,48 @@ __device__ inline void report_not_spd(Status *st, int scenario, int stage) {
 }
 
 // Root reduction of Alg. 1 step 4 for one entry (i, j): sum_s U_s[i][j] in
-// the library's fixed order -- four accumulators over s = k mod 4, each in
-// increasing s, combined as (a0 + a1) + (a2 + a3) -- so that every code path
-// (single system, batch) gets the same bits for the same system.
-__device__ inline double root_sum(const double *U, int S, int nr, int i, int j) {
-  double a[4] = {0.0, 0.0, 0.0, 0.0};
+// the library's fixed order. Lane l of a warp adds U_l, U_{l+32}, ... in
+// increasing s; the 32 partial sums p_l are then combined by the butterfly
+// p_l <- p_l + p_{l xor o} for o = 16, 8, 4, 2, 1 (addition commutes
+// exactly, so every lane ends with the same bits). Every code path (single
+// system, batch, serving) uses this order, so a system's root gets the same
+// bits wherever it is factored. Call with all 32 lanes of a warp.
+__device__ inline double root_sum_warp(const double *U, int S, int nr, int i, int j) {
+  const int lane = threadIdx.x & 31;
   const size_t stride = (size_t)nr * nr, off = (size_t)i * nr + j;
-  int s = 0;
-  // sixteen loads in flight per step; accumulator k still adds U[s + k],
-  // U[s + 4 + k], ... in increasing s, so the bits do not depend on the unroll
-  for (; s + 16 <= S; s += 16) {
-    double v[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) v[k] = __ldcg(U + (size_t)(s + k) * stride + off);
-#pragma unroll
-    for (int k = 0; k < 16; ++k) a[k & 3] += v[k];
+  double acc = 0.0;
+  int s = lane;
+  // four loads in flight per lane; each lane still adds in increasing s
+  for (; s + 96 < S; s += 128) {
+    const double a = __ldcg(U + (size_t)s * stride + off), b = __ldcg(U + (size_t)(s + 32) * stride + off);
+    const double c = __ldcg(U + (size_t)(s + 64) * stride + off), d = __ldcg(U + (size_t)(s + 96) * stride + off);
+    acc += a;
+    acc += b;
+    acc += c;
+    acc += d;
   }
-  for (; s + 4 <= S; s += 4) {
+  for (; s < S; s += 32) acc += __ldcg(U + (size_t)s * stride + off);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) a[k] += __ldcg(U + (size_t)(s + k) * stride + off);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  return acc;
+}
+
+// The same order evaluated by one thread.
+__device__ inline double root_sum_serial(const double *U, int S, int nr, int i, int j) {
+  const size_t stride = (size_t)nr * nr, off = (size_t)i * nr + j;
+  double p[32];
+#pragma unroll
+  for (int l = 0; l < 32; ++l) p[l] = 0.0;
+  for (int s = 0; s < S; ++s) p[s & 31] += __ldcg(U + (size_t)s * stride + off);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double q[32];
+#pragma unroll
+    for (int l = 0; l < 32; ++l) q[l] = p[l] + p[l ^ o];
+#pragma unroll
+    for (int l = 0; l < 32; ++l) p[l] = q[l];
   }
-  for (int k = 0; s < S; ++s, ++k) a[k] += __ldcg(U + (size_t)s * stride + off);
-  return (a[0] + a[1]) + (a[2] + a[3]);
+  return p[0];
 }
 
 // Views passed to the FP64 kernels (by value).

@@ -30,6 +30,7 @@
 
 #include <new>
 
+#include "bm_coupling.cuh"
 #include "bm_mixed.cuh"
 
 namespace bm {
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__(256) k_mixed_fwd(MixedState m, const double *_
   const int it = ir_iter(m.ctl, iter);
   const double *rhs = it == 0 ? r : m.rho;
   fwd_tail<NB>(m, rhs, blockIdx.x / CS, (int)cluster_rank(), CS, sY);
-  if (last_cta(&m.tickets[2], gridDim.x)) root_step<NB>(m, rhs, x, it, sR);
+  if (last_cta(&m.tickets[2], gridDim.x)) root_step<NB>(m, rhs, x, it, sR, coupled(m) ? m.S * CS : m.S);
 }
 
 template <int NB>
@@ -202,7 +203,12 @@ cudaError_t capture_loop(const MixedState &m, const double *r, double *x, int ma
 
 }  // namespace
 
-size_t mixed_bytes(int S, int N, int nb, int nr) {
+// Columns of the coupling vectors (nr rounded up to the register chunk).
+static int coupling_ldc(int nr) { return (nr + cx::RC - 1) / cx::RC * cx::RC; }
+
+// cmode: 0 = the FP32-based root (no coupling buffers), 1 = automatic,
+// 2 = always refine the coupling columns.
+size_t mixed_bytes(int S, int N, int nb, int nr, int cmode) {
   const size_t SN = (size_t)S * N, b2 = (size_t)nb * nb, n = SN * nb + nr;
   size_t t = 0;
   t += align_up(SN * b2 * sizeof(float), 256) * 5;          // Ld Ll Lr Dt W
@@ -210,12 +216,20 @@ size_t mixed_bytes(int S, int N, int nb, int nr) {
   t += align_up((size_t)S * nr * nb * sizeof(double), 256); // F
   t += align_up((size_t)S * nr * nr * sizeof(double), 256); // U
   t += align_up((size_t)nr * nr * sizeof(double), 256) * 2; // LR Rt
-  t += align_up((size_t)S * nr * sizeof(double), 256);      // tb
+  t += align_up((size_t)S * nr * sizeof(double) * (cmode ? 8 : 1), 256);  // tb
   t += align_up((size_t)nr * sizeof(double), 256);          // d0
   t += align_up(n * sizeof(double), 256);                   // rho
   t += align_up(sizeof(IRCtl), 256);
+  if (cmode) {
+    const int ldc = coupling_ldc(nr);
+    const size_t xb = align_up(SN * nb * ldc * sizeof(float), 256);
+    t += xb;                          // Xa
+    if (ldc > nb) t += 2 * xb;        // Yb, Zr (else they reuse W and Dt)
+  }
   return t;
 }
+
+size_t mixed_bytes(int S, int N, int nb, int nr) { return mixed_bytes(S, N, nb, nr, 0); }
 
 cudaError_t mixed_prepare(int nb, int nr) {
   (void)nr;
@@ -223,9 +237,9 @@ cudaError_t mixed_prepare(int nb, int nr) {
   return tail_factor_prepare();
 }
 
-MixedState *mixed_create(int S, int N, int nb, int nr, void *base, size_t bytes, Status *status,
+MixedState *mixed_create(int S, int N, int nb, int nr, int cmode, void *base, size_t bytes, Status *status,
                          unsigned *tickets, cudaStream_t init_stream, bool sync_init) {
-  if (bytes < mixed_bytes(S, N, nb, nr)) return nullptr;
+  if (bytes < mixed_bytes(S, N, nb, nr, cmode)) return nullptr;
   MixedState *m = new (std::nothrow) MixedState();
   if (!m) return nullptr;
   m->S = S; m->N = N; m->nb = nb; m->nr = nr; m->Lc = chain_levels(N);
@@ -241,9 +255,24 @@ MixedState *mixed_create(int S, int N, int nb, int nr, void *base, size_t bytes,
   m->invd = (float *)take(SN * nb * 4); m->y = (float *)take(SN * nb * 4); m->zt = (float *)take(SN * nb * 4);
   m->F = (double *)take((size_t)S * nr * nb * 8); m->U = (double *)take((size_t)S * nr * nr * 8);
   m->LR = (double *)take((size_t)nr * nr * 8); m->Rt = (double *)take((size_t)nr * nr * 8);
-  m->tb = (double *)take((size_t)S * nr * 8); m->d0 = (double *)take((size_t)nr * 8);
+  m->tb = (double *)take((size_t)S * nr * 8 * (cmode ? 8 : 1)); m->d0 = (double *)take((size_t)nr * 8);
   m->rho = (double *)take(n * 8);
   m->ctl = (IRCtl *)take(sizeof(IRCtl));
+  m->cmode = cmode;
+  m->cxon = &status->coupled;
+  if (cmode) {
+    m->ldc = coupling_ldc(nr);
+    const size_t xb = SN * nb * m->ldc * 4;
+    m->Xa = (float *)take(xb);
+    m->Xc = m->Xa;
+    if (m->ldc > nb) {
+      m->Yb = (float *)take(xb);
+      m->Zr = (float *)take(xb);
+    } else {
+      m->Yb = m->W;
+      m->Zr = m->Dt;
+    }
+  }
   m->status = status;
   m->tickets = tickets;
   if ((sync_init ? cudaMemset(m->ctl, 0, sizeof(IRCtl)) : cudaMemsetAsync(m->ctl, 0, sizeof(IRCtl), init_stream)) !=
@@ -258,7 +287,8 @@ void mixed_destroy(MixedState *m) { delete m; }
 
 // Root step of the factor, shared with the FP64 path (bm_fp64.cu).
 void f64_launch_factor_root_raw(int S, int nr, const double *U, const double *R, double *Rt, double *LR,
-                                unsigned *tickets, Status *status, cudaStream_t st);
+                                unsigned *tickets, Status *status, int mode, int *on, cudaStream_t st);
+void coupling_launch(const cx::CxView &v, int nb, int *mark, cudaStream_t st);
 
 void mixed_launch_factor(MixedState *m, const double *D, const double *E, const double *C, const double *R,
                          cudaStream_t st) {
@@ -269,7 +299,24 @@ void mixed_launch_factor(MixedState *m, const double *D, const double *E, const 
   t.Ld = m->Ld; t.Ll = m->Ll; t.Lr = m->Lr; t.Dt = m->Dt; t.W = m->W; t.invd = m->invd;
   t.F = m->F; t.U = m->U; t.status = m->status;
   tail_factor_launch<float>(t, st);
-  f64_launch_factor_root_raw(m->S, m->nr, m->U, R, m->Rt, m->LR, m->tickets, m->status, st);
+  int *on = &m->status->coupled;
+  if (m->cmode == 0) {
+    f64_launch_factor_root_raw(m->S, m->nr, m->U, R, m->Rt, m->LR, m->tickets, m->status, 0, nullptr, st);
+    return;
+  }
+  // automatic mode: the FP32-based root decides whether the coupling
+  // columns are refined (and is final when they are not)
+  if (m->cmode == 1)
+    f64_launch_factor_root_raw(m->S, m->nr, m->U, R, m->Rt, m->LR, m->tickets, m->status, 1, on, st);
+  cx::CxView cv;
+  cv.S = m->S; cv.N = m->N; cv.nr = m->nr; cv.ldc = m->ldc; cv.Lc = m->Lc;
+  cv.Ld = m->Ld; cv.Ll = m->Ll; cv.Lr = m->Lr; cv.invd = m->invd;
+  cv.D = D; cv.E = E; cv.C = C;
+  cv.Xa = m->Xa; cv.Yb = m->Yb; cv.Zr = m->Zr; cv.U = m->U;
+  cv.on = m->cmode == 1 ? on : nullptr;
+  coupling_launch(cv, m->nb, m->cmode == 2 ? on : nullptr, st);
+  f64_launch_factor_root_raw(m->S, m->nr, m->U, R, m->Rt, m->LR, m->tickets, m->status, m->cmode == 1 ? 2 : 0, on,
+                             st);
 }
 
 cudaError_t mixed_launch_solve(MixedState *m, const double *r, double *x, int max_refine, double tol,

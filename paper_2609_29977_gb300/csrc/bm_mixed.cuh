@@ -2,6 +2,7 @@
 // system kernels (bm_mixed.cu) and the batched kernels (bm_batch.cu).
 #pragma once
 
+#include "bm_ff.cuh"
 #include "bm_tail_factor.cuh"
 
 namespace bm {
@@ -20,8 +21,16 @@ struct MixedState {
   float *Ld, *Ll, *Lr, *Dt, *W, *invd;   // FP32 tail factor and level workspace
   double *F, *U, *LR, *Rt;               // FP64 root parts
   float *y, *zt;                         // [S][N][nb] solve vectors (y is overwritten by the correction)
-  double *tb;                            // [S][nr]
+  double *tb;                            // [S * 8][nr] per-tail (or per-CTA) root terms
   double *d0;                            // [nr] root correction
+  // refined coupling columns X_i = K_i^{-1} C_i^T ([S][N][nb][ldc], FP32;
+  // bm_coupling.cuh), used by the solve when *cxon is set; null when the
+  // handle never refines them
+  const float *Xc;
+  int ldc;
+  const int *cxon;
+  int cmode;                             // 0: FP32-based root, 1: automatic, 2: always refine
+  float *Xa, *Yb, *Zr;                   // coupling refinement buffers (Xa = Xc)
   double *rho;                           // [n] residual
   IRCtl *ctl;
   Status *status;
@@ -142,6 +151,69 @@ __device__ __forceinline__ void load_row(float (&r)[NB], const float *__restrict
   }
 }
 
+// The solve uses the refined coupling columns (bm_coupling.cuh).
+__device__ __forceinline__ bool coupled(const MixedState &m) {
+  return m.Xc != nullptr && *((volatile const int *)m.cxon) != 0;
+}
+
+// Root term of tail s with refined coupling columns: X_i^T rhs_i over the
+// rows of the tail that this CTA of its cluster covers (all of them when
+// CS = 1), written to tb[s * CS + crank]. Each product enters a Dot2 sum
+// (rhs split into hi + lo floats, X_i exactly FP32); the per-thread pairs
+// are combined by a fixed warp butterfly and then over the warps in order,
+// so the bits do not depend on timing.
+__device__ __forceinline__ void xt_rhs_partial(const MixedState &m, const double *__restrict__ rhs, int NBr, int s,
+                                               int crank, int CS) {
+  __shared__ float sph[8][8], spl[8][8];
+  const int rows = m.N * NBr, nr = m.nr, ldc = m.ldc;
+  const size_t base = (size_t)s * rows;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int c0 = 0; c0 < nr; c0 += 8) {
+    float h[8], l[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) h[c] = l[c] = 0.0f;
+    for (int rr = crank * blockDim.x + threadIdx.x; rr < rows; rr += CS * blockDim.x) {
+      float rh, rl;
+      ff::split_d(rhs[base + rr], rh, rl);
+      const float *xr = m.Xc + (base + rr) * ldc + c0;
+      const float4 a = __ldcg(reinterpret_cast<const float4 *>(xr));
+      const float4 b = __ldcg(reinterpret_cast<const float4 *>(xr + 4));
+      const float xv[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int c = 0; c < 8; ++c) ff::dot2_step_split(h[c], l[c], rh, rl, xv[c]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const float hh = __shfl_xor_sync(0xffffffffu, h[c], o), ll = __shfl_xor_sync(0xffffffffu, l[c], o);
+        float e;
+        ff::two_sum(h[c], hh, h[c], e);
+        l[c] = __fadd_rn(l[c], __fadd_rn(ll, e));
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        sph[warp][c] = h[c];
+        spl[warp][c] = l[c];
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < 8 && c0 + (int)threadIdx.x < nr) {
+      const int c = threadIdx.x;
+      float hs = sph[0][c], ls = spl[0][c];
+      for (int w = 1; w < nw; ++w) {
+        float e;
+        ff::two_sum(hs, sph[w][c], hs, e);
+        ls = __fadd_rn(ls, __fadd_rn(spl[w][c], e));
+      }
+      m.tb[((size_t)s * CS + crank) * nr + c0 + c] = ff::to_double(hs, ls);
+    }
+    __syncthreads();
+  }
+}
+
 // Forward substitution of one tail in FP32 (all levels, then x_1 and
 // t_i = F_{i,1} y_1 in FP64); the last CTA of the grid does the root step
 // of Alg. 2 in FP64 and stores the root correction d_0 (and x_0 += d_0).
@@ -153,6 +225,8 @@ __device__ __forceinline__ void fwd_tail(const MixedState &m, const double *__re
   const int N = m.N, Lc = m.Lc;
   const size_t sb = (size_t)s * N;
   const int i = tm.lane;
+  const bool xmode = coupled(m);
+  if (xmode) xt_rhs_partial(m, rhs, NB, s, crank, CS);
   for (int lvl = 0; lvl <= Lc; ++lvl) {
     const bool lastlvl = lvl == Lc;
     const int ntask = lastlvl ? 1 : (lvl == 0 ? N / 2 : ((N - 1) >> lvl) + 1);
@@ -223,7 +297,7 @@ __device__ __forceinline__ void fwd_tail(const MixedState &m, const double *__re
         }
       }
       if (i < NB) m.y[zoff + i] = z;
-      if (lastlvl) {
+      if (lastlvl && !xmode) {
         tm.sync();
         const int nr = m.nr;
         const double *Fs = m.F + (size_t)s * nr * NB;
@@ -243,21 +317,26 @@ __device__ __forceinline__ void fwd_tail(const MixedState &m, const double *__re
   }
 }
 
-// Root step of Alg. 2 for one system, by one CTA once every tail's
-// t_i = F_{i,1} y_1 is in tb: r~_0 = rhs_0 - sum_i t_i (fixed order),
-// d_0 = L_R^{-T} L_R^{-1} r~_0 (FP64), x_0 += d_0.
+// Root step of Alg. 2 for one system, by one CTA once every tail's root
+// term is in tb (t_i = F_{i,1} y_1, or with refined coupling columns the
+// per-CTA parts of X_i^T rhs_i; nt entries): r~_0 = rhs_0 - sum_t tb_t,
+// d_0 = L_R^{-T} L_R^{-1} r~_0 (FP64), x_0 += d_0. The sum over t is fixed
+// in order: lane l of a warp adds the entries t = l, l + 32, ... in
+// increasing t, and the 32 partial sums are combined by a fixed butterfly.
 template <int NB>
 __device__ __forceinline__ void root_step(const MixedState &m, const double *__restrict__ rhs, double *x, int iter,
-                                          double *sR) {
+                                          double *sR, int nt) {
   const int N = m.N, nr = m.nr, S = m.S;
   const size_t n0 = (size_t)S * N * NB;
-  double *sL = sR, *sz = sR + nr * nr, *sInv = sz + nr;
+  double *sL = sR, *sz = sR + nr * nr;
   for (int e = threadIdx.x; e < nr * nr; e += blockDim.x) sL[e] = __ldcg(m.LR + e);
-  // r~_0 = rhs_0 - sum_i t_i, fixed summation order per component
-  for (int c = threadIdx.x; c < nr; c += blockDim.x) {
-    double acc = rhs[n0 + c];
-    for (int t = 0; t < S; ++t) acc -= __ldcg(m.tb + (size_t)t * nr + c);
-    sz[c] = acc;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int c = warp; c < nr; c += nw) {
+    double acc = 0.0;
+    for (int t = lane; t < nt; t += 32) acc += __ldcg(m.tb + (size_t)t * nr + c);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) sz[c] = rhs[n0 + c] - acc;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -276,7 +355,6 @@ __device__ __forceinline__ void root_step(const MixedState &m, const double *__r
       x[n0 + j] = (iter == 0 ? 0.0 : x[n0 + j]) + sz[j];
     }
   }
-  (void)sInv;
 }
 
 // Last-CTA election over n participating CTAs with the counter *ticket
@@ -304,6 +382,13 @@ __device__ __forceinline__ void bwd_tail(const MixedState &m, double *x, int ite
   const int N = m.N, Lc = m.Lc, nr = m.nr;
   const size_t sb = (size_t)s * N;
   const int i = tm.lane;
+  const bool xmode = coupled(m);
+  // d_0 as hi + lo floats for the tails' X_i d_0 (refined coupling columns)
+  __shared__ float sdh[64], sdl[64];
+  if (xmode) {
+    for (int c = threadIdx.x; c < nr; c += blockDim.x) ff::split_d(__ldcg(m.d0 + c), sdh[c], sdl[c]);
+    __syncthreads();
+  }
   for (int lvl = Lc; lvl >= 0; --lvl) {
     const bool first = lvl == Lc;
     const int ntask = first ? 1 : (((N - 1) >> lvl) + 1) / 2;
@@ -323,7 +408,9 @@ __device__ __forceinline__ void bwd_tail(const MixedState &m, double *x, int ite
       }
       float z = 0.0f;
       if (i < NB) {
-        if (first) {
+        if (first && xmode) {
+          z = m.y[zoff + i];
+        } else if (first) {
           double zd = f2d_exact(m.y[zoff + i]);
           const double *Fs = m.F + (size_t)s * nr * NB;
           for (int c = 0; c < nr; ++c) zd = fma(-Fs[c * NB + i], __ldcg(m.d0 + c), zd);
@@ -363,7 +450,18 @@ __device__ __forceinline__ void bwd_tail(const MixedState &m, double *x, int ite
       }
       if (i < NB) {
         m.y[zoff + i] = z;
-        const double dz = f2d_exact(z);
+        double dz;
+        if (xmode) {
+          // d_i = z - X_i d_0 on this row, the product summed by Dot2
+          const float *xr = m.Xc + (zoff + i) * m.ldc;
+          float h = 0.0f, l = 0.0f;
+          for (int c = 0; c < nr; ++c) ff::dot2_step_split(h, l, sdh[c], sdl[c], __ldcg(xr + c));
+          float dh, e;
+          ff::two_sum(z, -h, dh, e);
+          dz = ff::to_double(dh, __fsub_rn(e, l));
+        } else {
+          dz = f2d_exact(z);
+        }
         x[zoff + i] = iter == 0 ? dz : x[zoff + i] + dz;
       }
       tm.sync();

@@ -1,6 +1,8 @@
 // Dispatch of the tail factorization on the block size (Alg. 1, steps 1-3).
 // The kernels are defined in bm_tail_factor.cuh and instantiated in
 // bm_tail_inst_*.cu.
+#include <mutex>
+
 #include "bm_tail_factor.cuh"
 #include "bm_tail_rows.cuh"
 
@@ -35,7 +37,9 @@ bool tail_nb_supported(int nb) {
 }
 
 cudaError_t tail_factor_prepare() {
+  static std::mutex mu;
   static bool done[64] = {false};
+  std::lock_guard<std::mutex> lock(mu);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorUnknown;
   if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;

@@ -1,8 +1,10 @@
 """The kernel counts the bench reports (``gpu_launches``), checked on CPU
 against counts taken by hand from the launch sequence of the library:
 factor = one launch per level below the top level, one top launch, one
-root launch; FP64 solve = forward, root, backward; mixed solve = three
-kernels per refinement iteration."""
+root launch; FP64 solve = forward, root, backward; mixed factor = the tail
+launches plus the root (FP32-based root), plus four coupling-column
+launches (always refined), plus a probing root (automatic); mixed solve =
+three kernels per refinement iteration."""
 from paper_2609_29977_gb300 import bm as core
 
 
@@ -27,10 +29,20 @@ def test_fp64_counts():
 
 
 def test_mixed_counts():
-    # medium, 2 corrections in a captured graph: 6 factor + 3 x 3 solve
-    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2) == 15
+    fp32 = core.BM_FLAG_COUPLING_FP32
+    # medium, FP32-based root, 2 corrections in a captured graph: 6 factor + 3 x 3 solve
+    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2, flags=fp32) == 15
     # directly launched: all 11 iterations
-    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10) == 6 + 33
+    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, flags=fp32) == 6 + 33
     # max_refine <= 0 selects 10; the count never exceeds max_refine + 1 iterations
-    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 0) == 6 + 33
-    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 3, iters=7) == 6 + 12
+    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 0, flags=fp32) == 6 + 33
+    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 3, iters=7, flags=fp32) == 6 + 12
+    # refined coupling columns: 5 tail launches (top level 4 of N = 64),
+    # bwd X0, residual, fwd, bwd correction, root
+    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2,
+                                  flags=core.BM_FLAG_COUPLING_REFINE) == 10 + 9
+    # automatic (default): probing root in addition
+    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2) == 11 + 9
+    # the mixed workload (N = 128: levels 0..6, top level 5): 6 tail launches
+    assert core.top_level(128) == 5
+    assert core.launches_per_step(512, 128, 24, 8, core.BM_PREC_FP32_IR, 8, iters=3) == 12 + 12
