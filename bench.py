@@ -717,7 +717,7 @@ def run_gpu(args):
     g = {k: v.to(dev) for k, v in sysd.items() if isinstance(v, torch.Tensor)}
     fl = bmgen.method_flops(w.S, w.N, w.nb, w.nr)
     solver = bm.BranchKKTSolver(w.S, w.N, w.nb, w.nr, precision=prec, max_refine=args.max_refine,
-                                tol=args.tol, flags=bm.BM_FLAG_NO_GRAPH if args.direct else 0)
+                                tol=args.tol, flags=(bm.BM_FLAG_NO_GRAPH if args.direct else 0) | _coupling_flags(args))
     x = torch.empty_like(g["r"])
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -872,7 +872,7 @@ def run_gpu(args):
     if args.precision == "fp64" and not args.no_fp32ir_compare:
         # the FP32-tail + FP64-refinement path on the same system, same timing
         mixed = bm.BranchKKTSolver(w.S, w.N, w.nb, w.nr, precision=bm.BM_PREC_FP32_IR,
-                                   max_refine=args.max_refine, tol=args.tol)
+                                   max_refine=args.max_refine, tol=args.tol, flags=_coupling_flags(args))
         xm = torch.empty_like(g["r"])
         for _ in range(max(3, args.warmup)):
             mixed.factor(g["D"], g["E"], g["C"], g["R"])
@@ -916,6 +916,11 @@ def run_gpu(args):
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+def _coupling_flags(args):
+    import paper_2609_29977_gb300 as bm
+    return {"auto": 0, "refine": bm.BM_FLAG_COUPLING_REFINE, "fp32": bm.BM_FLAG_COUPLING_FP32}[args.coupling]
 
 
 def _sub_line(fn):
@@ -971,6 +976,8 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=160.0, help="serving: HBM arena")
     ap.add_argument("--seed", type=int, default=2000)
     ap.add_argument("--gen-device", default="cuda", help="batched: where the systems are drawn (cuda or cpu)")
+    ap.add_argument("--coupling", default="auto", choices=["auto", "refine", "fp32"],
+                    help="mixed precision: refine the coupling columns automatically, always, or never")
     ap.add_argument("--no-forms", action="store_true",
                     help="default workload: skip the batched and serving sub-runs reported beside the main line")
     args = ap.parse_args()

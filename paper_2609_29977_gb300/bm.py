@@ -231,8 +231,10 @@ def launches_per_step(S, N, nb, nr, precision=BM_PREC_FP64, max_refine=10, iters
     BM_FLAG_COUPLING_FP32 the root; with BM_FLAG_COUPLING_REFINE the four
     coupling-column launches and the root; by default the probing root, the
     four coupling-column launches and a second root (the last five return at
-    once when the probe does not engage the refinement). Mixed solve: three
-    kernels per refinement iteration; pass the corrections of the solve
+    once when the probe does not engage the refinement). Mixed solve: with
+    coupling columns (both modes but BM_FLAG_COUPLING_FP32) one launch for
+    the first correction's root terms, then three kernels per refinement
+    iteration; pass the corrections of the solve
     (``query()["iters"]``) for a captured graph, whose loop stops after the
     last iteration that runs; without it the count is the unrolled
     direct-launch bound (``max_refine <= 0`` selects 10)."""
@@ -241,12 +243,11 @@ def launches_per_step(S, N, nb, nr, precision=BM_PREC_FP64, max_refine=10, iters
         mr = max_refine if max_refine > 0 else 10
         runs = mr + 1 if iters is None else min(int(iters), mr) + 1
         if flags & BM_FLAG_COUPLING_FP32:
-            factor = top_level(N) + 2
-        elif flags & BM_FLAG_COUPLING_REFINE:
-            factor = top_level(N) + 6
-        else:
-            factor = top_level(N) + 7
-        return factor + 3 * runs
+            return (top_level(N) + 2) + 3 * runs
+        # refined coupling columns: the first correction's root terms are
+        # one more launch per solve (it returns at once when not refined)
+        factor = top_level(N) + (6 if flags & BM_FLAG_COUPLING_REFINE else 7)
+        return factor + 1 + 3 * runs
     if nb not in TAIL_NB:
         return (Lc + 2) + (2 * Lc + 3)
     return (top_level(N) + 2) + 3

@@ -56,11 +56,12 @@ int pick_cluster_cx(int S) {
 }
 
 template <typename... KArgs, typename... Args>
-cudaError_t launch_cx(void (*kern)(KArgs...), unsigned grid, int CS, cudaStream_t st, Args... args) {
+cudaError_t launch_cx_shape(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, int CS,
+                            cudaStream_t st, Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(256);
-  cfg.dynamicSmemBytes = 0;
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -72,6 +73,11 @@ cudaError_t launch_cx(void (*kern)(KArgs...), unsigned grid, int CS, cudaStream_
   cfg.attrs = attr;
   cfg.numAttrs = CS > 1 ? 2 : 1;
   return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_cx(void (*kern)(KArgs...), unsigned grid, int CS, cudaStream_t st, Args... args) {
+  return launch_cx_shape(kern, grid, 256, 0, CS, st, args...);
 }
 
 template <int NB>

@@ -28,6 +28,7 @@
 // bitwise identical.
 #include <cuda_runtime.h>
 
+#include <mutex>
 #include <new>
 
 #include "bm_coupling.cuh"
@@ -36,6 +37,17 @@
 namespace bm {
 namespace {
 using namespace mx;
+
+// CTAs of the residual and root-term launches (grid-stride over the rows of
+// the tails, at least one CTA per root row): also the number of root-term
+// parts the forward kernel sums. At most max(152 * 8, nr).
+__host__ __device__ inline int xt_blocks(int S, int N, int nb, int nr) {
+  const long rows = (long)S * N * nb;
+  long blocks = (rows + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks < nr) blocks = nr;
+  return (int)blocks;
+}
 
 // iter >= 0: a directly launched iteration; iter < 0: the body of a graph
 // loop, whose iteration index is read from the control block and whose
@@ -52,7 +64,7 @@ __global__ void __launch_bounds__(256) k_mixed_fwd(MixedState m, const double *_
   const int it = ir_iter(m.ctl, iter);
   const double *rhs = it == 0 ? r : m.rho;
   fwd_tail<NB>(m, rhs, blockIdx.x / CS, (int)cluster_rank(), CS, sY);
-  if (last_cta(&m.tickets[2], gridDim.x)) root_step<NB>(m, rhs, x, it, sR, coupled(m) ? m.S * CS : m.S);
+  if (last_cta(&m.tickets[2], gridDim.x)) root_step<NB>(m, rhs, x, it, sR, coupled(m) ? xt_blocks(m.S, m.N, NB, m.nr) : m.S);
 }
 
 template <int NB>
@@ -66,7 +78,9 @@ __global__ void __launch_bounds__(256) k_mixed_bwd(MixedState m, double *x, int 
 // rho = r - K x in FP64 and the componentwise backward error of the
 // iterate; one thread per row of the tails (grid-stride; every lane of an
 // FP64 warp instruction does useful work), one more CTA-strided pass over
-// the root rows. The last CTA applies the stopping test.
+// the root rows. With refined coupling columns each CTA then leaves its part
+// of the next correction's root term X^T rho in tb. The last CTA applies
+// the stopping test.
 template <int NB>
 __global__ void __launch_bounds__(256) k_mixed_residual(MixedState m, const double *__restrict__ r,
                                                          const double *__restrict__ x, int iter, int max_iter,
@@ -84,6 +98,8 @@ __global__ void __launch_bounds__(256) k_mixed_residual(MixedState m, const doub
     om = fmaxf(om, residual_row<NB>(m, r, x, s, k, i));
   }
   omega_publish(m.ctl, om);
+  // each thread reads back only the rho rows it wrote
+  if (coupled(m)) xt_grid(m, m.rho, NB);
   // root rows; their omega goes through the same maximum
   if (threadIdx.x == 0) sroot = 0u;
   __syncthreads();
@@ -97,6 +113,16 @@ __global__ void __launch_bounds__(256) k_mixed_residual(MixedState m, const doub
     const bool more = ir_stop(m, 0.0f, it, max_iter, tol);
     if (iter < 0 && more) cudaGraphSetConditional(cond, 1u);
   }
+}
+
+// Root terms of the first correction with refined coupling columns: the
+// per-CTA parts of X^T r over the same grid-stride walk as the residual
+// kernel (which leaves those of the later corrections). Returns at once
+// without refined columns.
+template <int NB>
+__global__ void __launch_bounds__(256) k_mixed_xt(MixedState m, const double *__restrict__ r) {
+  pdl_wait();
+  if (coupled(m)) xt_grid(m, r, NB);
 }
 
 // Widen the FP32 tail factor for export.
@@ -133,11 +159,12 @@ void launch_cluster(void (*kern)(KArgs...), unsigned grid, unsigned block, int C
 }
 
 template <typename... KArgs, typename... Args>
-void launch_plain(void (*kern)(KArgs...), unsigned grid, unsigned block, bool pdl, cudaStream_t st, Args... args) {
+void launch_plain(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, bool pdl, cudaStream_t st,
+                  Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -155,11 +182,8 @@ void launch_iteration(const MixedState &m, const double *r, double *x, int iter,
   const unsigned grid = (unsigned)(m.S * CS);
   launch_cluster(k_mixed_fwd<NB>, grid, 256, CS, pdl, st, m, r, x, iter, CS, cond);
   launch_cluster(k_mixed_bwd<NB>, grid, 256, CS, pdl, st, m, x, iter, CS);
-  const long rows = (long)m.S * m.N * NB;
-  long blocks = (rows + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
-  if (blocks < m.nr) blocks = m.nr;
-  launch_plain(k_mixed_residual<NB>, (unsigned)blocks, 256, pdl, st, m, r, (const double *)x, iter, max_iter, tol,
+  const int blocks = xt_blocks(m.S, m.N, NB, m.nr);
+  launch_plain(k_mixed_residual<NB>, (unsigned)blocks, 256, 0, pdl, st, m, r, (const double *)x, iter, max_iter, tol,
                cond);
 }
 
@@ -216,7 +240,7 @@ size_t mixed_bytes(int S, int N, int nb, int nr, int cmode) {
   t += align_up((size_t)S * nr * nb * sizeof(double), 256); // F
   t += align_up((size_t)S * nr * nr * sizeof(double), 256); // U
   t += align_up((size_t)nr * nr * sizeof(double), 256) * 2; // LR Rt
-  t += align_up((size_t)S * nr * sizeof(double) * (cmode ? 8 : 1), 256);  // tb
+  t += align_up((size_t)nr * sizeof(double) * (cmode && S < 152 * 8 ? 152 * 8 : S), 256);  // tb (grid parts <= max(1216, nr <= 64))
   t += align_up((size_t)nr * sizeof(double), 256);          // d0
   t += align_up(n * sizeof(double), 256);                   // rho
   t += align_up(sizeof(IRCtl), 256);
@@ -231,10 +255,19 @@ size_t mixed_bytes(int S, int N, int nb, int nr, int cmode) {
 
 size_t mixed_bytes(int S, int N, int nb, int nr) { return mixed_bytes(S, N, nb, nr, 0); }
 
+
 cudaError_t mixed_prepare(int nb, int nr) {
   (void)nr;
   if (!tail_nb_supported(nb)) return cudaErrorInvalidValue;
-  return tail_factor_prepare();
+  static std::mutex mu;
+  static bool done[64] = {false};
+  std::lock_guard<std::mutex> lock(mu);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorUnknown;
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  cudaError_t e = tail_factor_prepare();
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+  return e;
 }
 
 MixedState *mixed_create(int S, int N, int nb, int nr, int cmode, void *base, size_t bytes, Status *status,
@@ -255,7 +288,7 @@ MixedState *mixed_create(int S, int N, int nb, int nr, int cmode, void *base, si
   m->invd = (float *)take(SN * nb * 4); m->y = (float *)take(SN * nb * 4); m->zt = (float *)take(SN * nb * 4);
   m->F = (double *)take((size_t)S * nr * nb * 8); m->U = (double *)take((size_t)S * nr * nr * 8);
   m->LR = (double *)take((size_t)nr * nr * 8); m->Rt = (double *)take((size_t)nr * nr * 8);
-  m->tb = (double *)take((size_t)S * nr * 8 * (cmode ? 8 : 1)); m->d0 = (double *)take((size_t)nr * 8);
+  m->tb = (double *)take((size_t)nr * 8 * (cmode && S < 152 * 8 ? 152 * 8 : S)); m->d0 = (double *)take((size_t)nr * 8);
   m->rho = (double *)take(n * 8);
   m->ctl = (IRCtl *)take(sizeof(IRCtl));
   m->cmode = cmode;
@@ -324,6 +357,16 @@ cudaError_t mixed_launch_solve(MixedState *m, const double *r, double *x, int ma
   // reset the per-solve control words
   cudaError_t e = cudaMemsetAsync(m->ctl, 0, sizeof(IRCtl), st);
   if (e != cudaSuccess) return e;
+  if (m->Xc) {
+    switch (m->nb) {
+#define X(n)                                                                                          \
+  case n:                                                                                             \
+    launch_plain(k_mixed_xt<n>, (unsigned)xt_blocks(m->S, m->N, n, m->nr), 256, 0, true, st, *m, r);          \
+    break;
+      BM_TAIL_NB_LIST(X)
+#undef X
+    }
+  }
   if (body_st) {
     switch (m->nb) {
 #define X(n) \

