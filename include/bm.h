@@ -70,13 +70,15 @@ typedef enum {
 /*
  * BM_PREC_FP32_IR only: how the root Schur complement R~ = R - sum_i U_i is
  * formed (Alg. 1 steps 3-4). By default (neither flag) the factor first
- * forms it from the FP32 tail factor; when that Cholesky fails, or some
- * diagonal entry cancels by more than 2^12 (R_jj > 4096 R~_jj), it refines
- * each tail's coupling columns X_i = K_i^{-1} C_i^T (the nr columns through
- * which the tail meets the root) with the FP32 factor and one FP64-accurate
- * residual, forms U_i = C_{i,1} X_i from them, refactors the root, and the
- * solves then use X_i for the root coupling. The flags force one choice.
- * Setting both is BM_ERR_INVALID_ARG.
+ * forms it from the FP32 tail factor. When that Cholesky fails, or the
+ * cancellation gamma = max_j R_jj / R~_jj times the FP32 factor's pivot
+ * spread rho = max over tails of (max_j L_jj / min_j L_jj)^2 times 2^-24
+ * exceeds 16 (the FP32-based R~ then has no correct digit to spare), it
+ * refines each tail's coupling columns X_i = K_i^{-1} C_i^T (the nr columns
+ * through which the tail meets the root) with the FP32 factor and one
+ * float-float residual, forms U_i = C_{i,1} X_i from them, refactors the
+ * root, and the solves then use X_i for the root coupling. The flags force
+ * one choice. Setting both is BM_ERR_INVALID_ARG.
  */
 #define BM_FLAG_COUPLING_REFINE 2u /* always refine the coupling columns */
 #define BM_FLAG_COUPLING_FP32 4u   /* never: R~ from the FP32 tail factor alone */
@@ -214,10 +216,12 @@ bm_status bm_factor_solve_host(bm_handle h, const double *hD, const double *hE,
  *     rejected with BM_ERR_INVALID_ARG before any work, as are the size
  *     limits of bm_analyze.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress, with that device current) and keeps it; make
- *     that first call before any stream capture.
+ *     (cudaGetSymbolAddress, with that device current) and keeps it.
  *   - The work is ordered on stream; the call then synchronizes stream and
  *     returns the device status (BM_ERR_NOT_SPD on a non-positive pivot).
+ *     It is synchronous and cannot be recorded into a CUDA graph: on a
+ *     stream that is being captured it returns BM_ERR_INVALID_ARG without
+ *     launching anything.
  *   - All calls share the one array, which keeps the last call's contents:
  *     two calls whose work overlaps on the GPU (different streams or host
  *     threads) race on it and must be serialized by the caller.

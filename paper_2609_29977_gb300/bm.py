@@ -229,9 +229,10 @@ def launches_per_step(S, N, nb, nr, precision=BM_PREC_FP64, max_refine=10, iters
     backward (generic kernels: one per level each way, plus x_1 forward,
     root and x_1 backward). Mixed factor: the tail launches, then with
     BM_FLAG_COUPLING_FP32 the root; with BM_FLAG_COUPLING_REFINE the four
-    coupling-column launches and the root; by default the probing root, the
-    four coupling-column launches and a second root (the last five return at
-    once when the probe does not engage the refinement). Mixed solve: with
+    coupling-column launches and the root; by default the pivot-spread
+    reduction, the probing root, the four coupling-column launches and a
+    second root (the last five return at once when the probe does not engage
+    the refinement). Mixed solve: with
     coupling columns (both modes but BM_FLAG_COUPLING_FP32) one launch for
     the first correction's root terms, then three kernels per refinement
     iteration; pass the corrections of the solve
@@ -246,7 +247,7 @@ def launches_per_step(S, N, nb, nr, precision=BM_PREC_FP64, max_refine=10, iters
             return (top_level(N) + 2) + 3 * runs
         # refined coupling columns: the first correction's root terms are
         # one more launch per solve (it returns at once when not refined)
-        factor = top_level(N) + (6 if flags & BM_FLAG_COUPLING_REFINE else 7)
+        factor = top_level(N) + (6 if flags & BM_FLAG_COUPLING_REFINE else 8)
         return factor + 1 + 3 * runs
     if nb not in TAIL_NB:
         return (Lc + 2) + (2 * Lc + 3)

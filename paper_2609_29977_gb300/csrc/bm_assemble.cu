@@ -18,6 +18,8 @@
 // depends on the launch shape.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "bm_internal.cuh"
 
 namespace bm {
@@ -138,9 +140,11 @@ extern "C" bm_status bm_assemble_reduced(const bm_qp_desc *d, const double *A, c
   cudaStream_t st = (cudaStream_t)stream;
   const int nb = d->nx + d->nu;
   const size_t smem = ((size_t)d->nx * nb + (size_t)nb * nb) * sizeof(double);
+  static std::mutex attr_mu;
   static bool attr_set[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> attr_lock(attr_mu);
   if (dev >= 0 && dev < 64 && !attr_set[dev]) {
     // the largest block (nb = 64, nx = 63) needs 64 KB of dynamic shared memory
     if (cudaFuncSetAttribute(k_assemble_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024) !=

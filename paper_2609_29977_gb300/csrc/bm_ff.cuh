@@ -78,39 +78,6 @@ __device__ __forceinline__ void split_d(double d, float &hi, float &lo) {
   }
 }
 
-// d = hi + lo with hi = d truncated to 24 significand bits and lo the FP32
-// rounding of the (same-signed) rest: |d - hi - lo| <= 2^-47 |d| for
-// 2^-103 <= |d| < 2^127, where lo is an FP32 normal number (below, lo
-// flushes to 0 and the error grows to 2^-23 |d|; outside the FP32 range hi
-// is the FP32 rounding). Fewer integer instructions than split_d; for sums
-// that carry their own rounding, where a correctly rounded hi buys nothing.
-__device__ __forceinline__ void split_trunc(double d, float &hi, float &lo) {
-  const unsigned whi = (unsigned)__double2hiint(d), wlo = (unsigned)__double2loint(d);
-  const unsigned e = (whi >> 20) & 0x7ffu;
-  if (e - 897u < 253u) {
-    const unsigned sign = whi & 0x80000000u;
-    hi = __uint_as_float(sign | ((e - 896u) << 23) | ((whi & 0x000fffffu) << 3) | (wlo >> 29));
-    const unsigned r = wlo & 0x1fffffffu;
-    const unsigned fb = __float_as_uint(__uint2float_rn(r));
-    const int fe = (int)((fb >> 23) & 0xffu) + (int)e - 1075;
-    lo = (r != 0u && fe > 0) ? __uint_as_float(sign | (fb & 0x007fffffu) | ((unsigned)fe << 23)) : 0.0f;
-  } else {
-    hi = d2f_rn(d);
-    lo = 0.0f;
-  }
-}
-
-// (s, c) += (ah + al) * (bh + bl), the products with a low part carried
-// only in c (they are at least 2^-23 below the leading product). al * bl is
-// kept: with truncating splits it has the sign of the product, so dropping
-// it would bias every term the same way.
-__device__ __forceinline__ void dot2_step_ff(float &s, float &c, float ah, float al, float bh, float bl) {
-  float p, ep, es;
-  two_prod(ah, bh, p, ep);
-  two_sum(s, p, s, es);
-  c = __fadd_rn(c, __fadd_rn(es, __fmaf_rn(al, bl, __fmaf_rn(ah, bl, __fmaf_rn(al, bh, ep)))));
-}
-
 // hi + lo as a double (exact).
 __device__ __forceinline__ double to_double(float hi, float lo) { return f2d_exact(hi) + f2d_exact(lo); }
 

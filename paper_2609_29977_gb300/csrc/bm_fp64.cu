@@ -251,20 +251,28 @@ __global__ void k_factor_x1(F64View v) {
   }
 }
 
-// Cancellation above which the automatic mode of the mixed path refines the
-// coupling columns: R_jj / R~_jj > 2^12 for some j means that the FP32-based
-// R~ keeps fewer than about three of the digits its terms U_i carry.
-constexpr double kRootCancelEngage = 4096.0;
+// Automatic mode of the mixed path: the coupling columns are refined when
+// the FP32-based root cannot be trusted. R~ = R - sum_i U_i loses the
+// digits of its cancellation gamma = max_j R_jj / R~_jj, and FP32 tails
+// give each U_i to about 2^-24 times their conditioning, which the FP32
+// factor's pivot spread rho = (max_j L_jj / min_j L_jj)^2 (per tail, max
+// over tails) bounds from below. Measured on the workloads (GB300 and the
+// oracle's factors): gamma * rho * 2^-24 is about 0.3-0.5 on the medium
+// workload and 4-9 on the large serving request, whose FP32-based roots
+// converge in 2-3 corrections, and 30-65 on the 10^+-6 mixed workload,
+// whose FP32-based root is indefinite or makes refinement diverge.
+constexpr double kRootEngage = 16.0;
 
 // Root: R~ = R - sum_i U_i (one warp per lower-triangle entry, fixed
 // summation order root_sum_warp), then L_R = chol(R~) by the last CTA to
 // finish (Alg. 1, steps 4-5).
 //  mode 0: plain.
 //  mode 1: probe of the mixed path's automatic mode, with FP32-based U_i:
-//          when the Cholesky fails or the diagonal cancels by more than
-//          kRootCancelEngage, *on = 1 (the refinement of the coupling
-//          columns then runs and a mode-2 launch redoes the root) and no
-//          failure is reported; else *on = 0 and this is the final root.
+//          when the Cholesky fails or gamma * rho * 2^-24 > kRootEngage
+//          (rho from the status word, left by k_pivot_spread), *on = 1 (the
+//          refinement of the coupling columns then runs and a mode-2
+//          launch redoes the root) and no failure is reported; else
+//          *on = 0 and this is the final root.
 //  mode 2: the root after that refinement; returns at once unless *on.
 __global__ void __launch_bounds__(256) k_factor_root(F64View v, int mode, int *on) {
   extern __shared__ double sm[];
@@ -292,9 +300,11 @@ __global__ void __launch_bounds__(256) k_factor_root(F64View v, int mode, int *o
   __syncthreads();
   bool engage = false;
   if (mode == 1) {
+    const double rho = (double)__uint_as_float(*((volatile const unsigned *)&v.status->spread));
+    const double lim = kRootEngage / (rho * 0x1.0p-24);
     for (int j = 0; j < nr; ++j) {
       const double rt = sR[j * nr + j];
-      if (!(rt > 0.0) || v.R[j * nr + j] > kRootCancelEngage * rt) engage = true;
+      if (!(rt > 0.0) || v.R[j * nr + j] > lim * rt) engage = true;
     }
   }
   __syncthreads();

@@ -60,7 +60,7 @@ struct Status {
   int stage;      // 1-based natural stage, 0 root
   int iters;      // refinement steps
   int coupled;    // mixed precision: the coupling columns were refined in the last factor
-  int pad_;
+  unsigned spread; // mixed precision: max over tails of (max/min FP32 pivot)^2, float bits
   double eta;     // refinement: componentwise backward error of the iterate
 };
 

@@ -125,6 +125,43 @@ __global__ void __launch_bounds__(256) k_mixed_xt(MixedState m, const double *__
   if (coupled(m)) xt_grid(m, r, NB);
 }
 
+// Pivot spread of the FP32 tail factor for the automatic mode's probe:
+// (max_j L_jj / min_j L_jj)^2 over the pivots of tail blockIdx.x (from the
+// inverse pivots invd), folded into the status word's maximum.
+__global__ void __launch_bounds__(256) k_pivot_spread(const float *__restrict__ invd, int N, int nb, Status *st) {
+  __shared__ float smax[8], smin[8];
+  pdl_wait();
+  const int rows = N * nb;
+  const float *p = invd + (size_t)blockIdx.x * rows;
+  float mx = 0.0f, mn = __int_as_float(0x7f800000);
+  for (int e = threadIdx.x; e < rows; e += blockDim.x) {
+    const float v = fabsf(p[e]);
+    mx = fmaxf(mx, v);
+    mn = fminf(mn, v);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    smax[threadIdx.x >> 5] = mx;
+    smin[threadIdx.x >> 5] = mn;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      mx = fmaxf(mx, smax[w]);
+      mn = fminf(mn, smin[w]);
+    }
+    mx = fmaxf(mx, smax[0]);
+    mn = fminf(mn, smin[0]);
+    const float ratio = mn > 0.0f ? (mx / mn) * (mx / mn) : __int_as_float(0x7f7fffff);
+    atomicMax(&st->spread, __float_as_uint(fminf(ratio, __int_as_float(0x7f7fffff))));
+  }
+  pdl_trigger();
+}
+
 // Widen the FP32 tail factor for export.
 __global__ void k_widen(const float *__restrict__ src, double *__restrict__ dst, size_t n) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -339,8 +376,10 @@ void mixed_launch_factor(MixedState *m, const double *D, const double *E, const 
   }
   // automatic mode: the FP32-based root decides whether the coupling
   // columns are refined (and is final when they are not)
-  if (m->cmode == 1)
+  if (m->cmode == 1) {
+    launch_plain(k_pivot_spread, (unsigned)m->S, 256, 0, true, st, (const float *)m->invd, m->N, m->nb, m->status);
     f64_launch_factor_root_raw(m->S, m->nr, m->U, R, m->Rt, m->LR, m->tickets, m->status, 1, on, st);
+  }
   cx::CxView cv;
   cv.S = m->S; cv.N = m->N; cv.nr = m->nr; cv.ldc = m->ldc; cv.Lc = m->Lc;
   cv.Ld = m->Ld; cv.Ll = m->Ll; cv.Lr = m->Lr; cv.invd = m->invd;

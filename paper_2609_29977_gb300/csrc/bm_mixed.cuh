@@ -496,11 +496,6 @@ __device__ __forceinline__ float omega_of(double rho, float w) {
 
 // Row i of block row (s, k) of the residual: rho_i = r_i - (K x)_i (stored
 // in m.rho) and its omega_i. Lanes i >= NB must not call it.
-// The sum is carried in float-float on the FP32 pipe (GB300's FP64 pipe
-// runs at 1/64 of it): every FP64 entry of K and x is split into hi + lo
-// floats (split_trunc) and the products enter a Dot2 sum (Ogita, Rump and
-// Oishi), so rho is exact to about 2^-46 of |K||x| + |r| -- four orders of
-// magnitude below the 1e-10 target, and 2^-7 above an FP64 sum's rounding.
 template <int NB>
 __device__ __forceinline__ float residual_row(const MixedState &m, const double *__restrict__ r,
                                               const double *__restrict__ x, int s, int k, int i) {
@@ -511,36 +506,42 @@ __device__ __forceinline__ float residual_row(const MixedState &m, const double 
   const size_t off = (size_t)br * NB;
   const double *Dk = m.D + (size_t)br * NB2;
   const double *xk = x + off;
-  float h, l;
-  ff::split_trunc(r[off + i], h, l);
-  float w = fabsf(h);
-  auto term = [&](double kij, double xj) {
-    float kh, kl, xh, xl;
-    ff::split_trunc(kij, kh, kl);
-    ff::split_trunc(xj, xh, xl);
-    ff::dot2_step_ff(h, l, -kh, -kl, xh, xl);
-    w = fmaf(fabsf(kh), fabsf(xh), w);
-  };
+  const double ri = r[off + i];
+  double acc = ri;
+  float w = abs_f32_approx(ri);
 #pragma unroll
-  for (int j = 0; j < NB; ++j) term(j <= i ? Dk[i * NB + j] : Dk[j * NB + i], xk[j]);
+  for (int j = 0; j < NB; ++j) {
+    const double kij = j <= i ? Dk[i * NB + j] : Dk[j * NB + i];
+    const double xj = xk[j];
+    acc = fma(-kij, xj, acc);
+    w = fmaf(abs_f32_approx(kij), abs_f32_approx(xj), w);
+  }
   if (k > 0) {   // block (k, k-1) = E_k (1-based stage k+1)
     const double *Ek = m.E + ((size_t)s * (N - 1) + (k - 1)) * NB2 + i * NB;
     const double *xp = xk - NB;
 #pragma unroll
-    for (int j = 0; j < NB; ++j) term(Ek[j], xp[j]);
+    for (int j = 0; j < NB; ++j) {
+      acc = fma(-Ek[j], xp[j], acc);
+      w = fmaf(abs_f32_approx(Ek[j]), abs_f32_approx(xp[j]), w);
+    }
   }
   if (k + 1 < N) {   // block (k, k+1) = E_{k+1}^T
     const double *Ek = m.E + ((size_t)s * (N - 1) + k) * NB2 + i;
     const double *xn = xk + NB;
 #pragma unroll
-    for (int j = 0; j < NB; ++j) term(Ek[j * NB], xn[j]);
+    for (int j = 0; j < NB; ++j) {
+      acc = fma(-Ek[j * NB], xn[j], acc);
+      w = fmaf(abs_f32_approx(Ek[j * NB]), abs_f32_approx(xn[j]), w);
+    }
   }
   if (k == 0) {   // block (1, root) = C_s^T
     const double *Cs = m.C + (size_t)s * nr * NB + i;
     const double *x0 = x + n0;
-    for (int j = 0; j < nr; ++j) term(Cs[j * NB], x0[j]);
+    for (int j = 0; j < nr; ++j) {
+      acc = fma(-Cs[j * NB], x0[j], acc);
+      w = fmaf(abs_f32_approx(Cs[j * NB]), abs_f32_approx(x0[j]), w);
+    }
   }
-  const double acc = ff::to_double(h, l);
   m.rho[off + i] = acc;
   return omega_of(acc, w);
 }

@@ -14,11 +14,14 @@
 // bytes: every GPU that loads the library holds it until the process exits.
 // In host code its name is only a host-side stand-in, so the first call on
 // each device looks up its device address with cudaGetSymbolAddress (with
-// that device current) and keeps it; make that first call before any
-// stream capture. All calls share the one array and it keeps the last
-// call's contents, so the status word and the cross-CTA counters are
-// cleared at the start of every call, and two calls whose work overlaps on
-// the GPU (different streams, or different host threads) race on it.
+// that device current) and keeps it. Every call ends by copying the device
+// status to the host and synchronizing the stream, so the entry point is
+// synchronous and cannot be recorded into a CUDA graph: on a stream that is
+// being captured it returns BM_ERR_INVALID_ARG before touching anything.
+// All calls share the one array and it keeps the last call's contents, so
+// the status word and the cross-CTA counters are cleared at the start of
+// every call, and two calls whose work overlaps on the GPU (different
+// streams, or different host threads) race on it.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -89,6 +92,12 @@ extern "C" bm_status bm_factor_solve_noalloc(int S, int N, int nb, int nr, const
   if (!D || !C || !R || !r || !x || (N > 1 && !E) || (const void *)r == (const void *)x)
     return BM_ERR_INVALID_ARG;
   if (noalloc_bytes(S, N, nb, nr) > (size_t)BM_NOALLOC_SCRATCH_BYTES) return BM_ERR_INVALID_ARG;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing((cudaStream_t)stream, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return BM_ERR_CUDA;
+  }
+  if (cap != cudaStreamCaptureStatusNone) return BM_ERR_INVALID_ARG;
   void *base = nullptr;
   bm_status s = scratch_on_current_device(&base);
   if (s != BM_OK) return s;

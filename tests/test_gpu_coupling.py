@@ -10,8 +10,9 @@ coupling of every solve. These tests check, against the FP64 oracle:
     at a bound set by the cancellation of the root block),
   * the solution (componentwise backward error omega <= tol of the oracle's
     own FP64 residual, forward error bounded by omega times cond(K)),
-  * the automatic choice (engaged exactly when the FP32-based root cancels
-    by more than 2^12 or is not positive definite),
+  * the automatic choice (engaged when the root's cancellation times the
+    FP32 factor's pivot spread times 2^-24 exceeds 16, or when the
+    FP32-based root is not positive definite),
   * graph and direct launches bit for bit, and repeatability.
 """
 import numpy as np
@@ -111,12 +112,12 @@ def test_refined_root_factor_matches_oracle(S, N, nb, nr, scale):
 
 
 def test_automatic_mode_engages_on_cancellation():
-    """Default flags: a root that cancels by 1e4 after FP32 tails engages the
-    refinement and converges; the same tails with a well-conditioned root do
-    not engage it."""
+    """Default flags: a root that cancels by 1.6e6 after these FP32 tails
+    (pivot spread about 3e3) engages the refinement and converges; the same
+    tails with a root that cancels by 1.6e2 do not engage it."""
     d_hi = gen(8, 24, 12, 4, seed=21, barrier=(-4, 4), shared_A=True, root_scale=1e-4)
     d_lo = gen(8, 24, 12, 4, seed=21, barrier=(-4, 4), shared_A=True)
-    assert cancellation(d_hi) > 4096 * 4 and cancellation(d_lo) < 4096 / 4
+    assert cancellation(d_hi) > 1e6 and cancellation(d_lo) < 1e3
     hi = run(d_hi)
     lo = run(d_lo)
     assert hi["info"]["coupling_refined"] == 1 and hi["info"]["status"] == 0, hi["info"]
@@ -161,7 +162,8 @@ def test_unresolvable_cancellation_is_reported():
 def test_refined_graph_and_direct_agree_bitwise(tol, max_refine):
     bm = _bm()
     d = gen(5, 31, 8, 9, seed=8, barrier=(-4, 4), shared_A=True, root_scale=1e-4)
-    outs = [run(d, tol=tol, max_refine=max_refine, direct=direct) for direct in (False, True)]
+    outs = [run(d, flags=bm.BM_FLAG_COUPLING_REFINE, tol=tol, max_refine=max_refine, direct=direct)
+            for direct in (False, True)]
     (a, b) = outs
     assert np.array_equal(a["x"], b["x"])
     for k in ("status", "iters", "backward_error", "coupling_refined"):

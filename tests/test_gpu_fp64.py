@@ -146,8 +146,9 @@ def test_fp64_plain_workload_parity():
 
 def test_fp64_medium_workload_full_size():
     """The medium FP64 workload at full size, in the launch configuration the
-    benchmark times (graphs on): x against the oracle, L_R exactly, and the
-    tail factors of sampled scenarios element by element."""
+    benchmark times (graphs on): x against the oracle (backward error, and
+    element by element within the condition-number bound), L_R exactly, and
+    the tail factors of sampled scenarios element by element."""
     w = bmgen.WORKLOADS["medium-s64-n64-nb12"]
     d = bmgen.generate(w)
     out = run_gpu(d)
@@ -156,6 +157,19 @@ def test_fp64_medium_workload_full_size():
     res, ref = check_solution(d, out["x"])
     nat = ref["fac"]
     assert np.allclose(out["fac"]["LR"], nat["LR"], rtol=0, atol=1e-9 * np.abs(nat["LR"]).max())
+    # x element by element against the oracle's x: two backward-stable FP64
+    # solves differ by at most about kappa_1(K) times the sum of their
+    # normwise backward errors (||K||_1 = ||K||_inf, K symmetric; ||K^-1||_1
+    # estimated by Higham's method through the oracle's own factor)
+    import scipy.sparse.linalg as spla
+    n = ref["x"].size
+    kinv = spla.LinearOperator((n, n), matvec=lambda v: natural.solve(nat, np.ascontiguousarray(v, dtype=np.float64)),
+                               rmatvec=lambda v: natural.solve(nat, np.ascontiguousarray(v, dtype=np.float64)),
+                               dtype=np.float64)
+    kappa = res["K_inf"] * spla.onenormest(kinv)
+    bound = 10.0 * kappa * (res["eta"] + ref["res"]["eta"]) + 1e-15
+    diff = np.abs(out["x"] - ref["x"]) / np.abs(ref["x"]).max()
+    assert diff.max() <= bound, (diff.max(), bound, kappa)
     # L_{i,1} of every tail against the Schur complement onto stage 1
     S1 = natural.tail_schur_first(d["D"], d["E"])
     L11 = out["fac"]["Ld"][:, 0]

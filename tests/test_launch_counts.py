@@ -3,7 +3,8 @@ against counts taken by hand from the launch sequence of the library:
 factor = one launch per level below the top level, one top launch, one
 root launch; FP64 solve = forward, root, backward; mixed factor = the tail
 launches plus the root (FP32-based root), plus four coupling-column
-launches (always refined), plus a probing root (automatic); mixed solve =
+launches (always refined), plus a pivot-spread reduction and a probing root
+(automatic); mixed solve =
 one root-term launch when coupling columns may be used, then three kernels
 per refinement iteration."""
 from paper_2609_29977_gb300 import bm as core
@@ -43,8 +44,8 @@ def test_mixed_counts():
     # correction's root terms
     assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2,
                                   flags=core.BM_FLAG_COUPLING_REFINE) == 10 + 1 + 9
-    # automatic (default): probing root in addition
-    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2) == 11 + 1 + 9
+    # automatic (default): pivot-spread reduction and probing root in addition
+    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2) == 12 + 1 + 9
     # the mixed workload (N = 128: levels 0..6, top level 5): 6 tail launches
     assert core.top_level(128) == 5
-    assert core.launches_per_step(512, 128, 24, 8, core.BM_PREC_FP32_IR, 8, iters=3) == 12 + 1 + 12
+    assert core.launches_per_step(512, 128, 24, 8, core.BM_PREC_FP32_IR, 8, iters=3) == 13 + 1 + 12
