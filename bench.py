@@ -78,10 +78,11 @@ def _factor_kernels(N, nb, precision):
     Lc, top = core.chain_levels(N), core.top_level(N)
     if precision == "fp64":
         if nb in core.TAIL_NB:
-            return "k_factor_level_team x%d + k_factor_top + k_factor_root" % top
+            return "k_factor_level_team x%d + k_factor_top (its last CTA does the root step)" % top
         return "k_factor_level x%d + k_factor_x1 + k_factor_root" % Lc
     suffix = "" if nb <= 32 else "_w"
-    return "k_level_rows%s x%d + k_top_rows%s + k_factor_root" % (suffix, top, suffix)
+    return ("k_level_rows%s x%d + k_top_rows%s + k_pivot_spread + k_factor_root (probe), then when refined "
+            "k_cx_bwd + k_cx_residual + k_cx_fwd + k_cx_bwd + k_factor_root" % (suffix, top, suffix))
 
 
 def _kernel_source_hash():

@@ -223,7 +223,8 @@ def launches_per_step(S, N, nb, nr, precision=BM_PREC_FP64, max_refine=10, iters
     """Kernels that one bm_factor + one bm_solve launch.
 
     Factor: one launch per level below ``top_level(N)``, one for the top
-    levels and x_1, one for the root (with the per-level generic kernels,
+    levels, x_1 and (FP64) the root, whose last CTA does the root step; the
+    mixed path launches the root separately (with the per-level generic kernels,
     used for block sizes without compiled tail kernels: one per level, one
     for x_1, one for the root). FP64 solve: tail forward, root, tail
     backward (generic kernels: one per level each way, plus x_1 forward,
@@ -251,7 +252,7 @@ def launches_per_step(S, N, nb, nr, precision=BM_PREC_FP64, max_refine=10, iters
         return factor + 1 + 3 * runs
     if nb not in TAIL_NB:
         return (Lc + 2) + (2 * Lc + 3)
-    return (top_level(N) + 2) + 3
+    return (top_level(N) + 1) + 3
 
 
 def make_desc(S, N, nb, nr, precision=BM_PREC_FP64, max_refine=10, tol=1e-10, flags=0) -> bm_desc:

@@ -137,7 +137,7 @@ __device__ void root_item(const BInst &I, const double *R, int lane, int TS, uns
 template <typename T>
 __device__ __forceinline__ TailView<T> tail_view(const BInst &I, const double *D, const double *E, const double *C,
                                                  const double *R) {
-  TailView<T> v;
+  TailView<T> v{};
   v.S = I.S; v.N = I.N; v.nb = I.nb; v.nr = I.nr; v.Lc = I.Lc;
   v.D = D; v.E = E; v.C = C; v.R = R;
   v.Ld = I.m.Ld; v.Ll = I.m.Ll; v.Lr = I.m.Lr; v.Dt = I.m.Dt; v.W = I.m.W; v.invd = I.m.invd;

@@ -28,7 +28,7 @@
 
 #include <mutex>
 
-#include "bm_internal.cuh"
+#include "bm_root.cuh"
 
 namespace bm {
 namespace {
@@ -47,24 +47,6 @@ __device__ __forceinline__ void cta_copy_t(double *__restrict__ dst, const doubl
 __device__ __forceinline__ void cta_zero(double *dst, int n) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = 0.0;
 }
-// global (n x n) := lower triangle of s, zeros above
-__device__ __forceinline__ void cta_store_lower(double *__restrict__ g, const double *__restrict__ s, int n) {
-  const int n2 = n * n;
-  for (int e = threadIdx.x; e < n2; e += blockDim.x) {
-    const int i = e / n, j = e - i * n;
-    g[e] = (j <= i) ? s[e] : 0.0;
-  }
-}
-
-// Lower-triangle element e -> (i, j) with j <= i.
-__device__ __forceinline__ void tri_ij(int e, int &i, int &j) {
-  int t = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-  while ((t + 1) * (t + 2) / 2 <= e) ++t;
-  while (t * (t + 1) / 2 > e) --t;
-  i = t;
-  j = e - t * (t + 1) / 2;
-}
-
 // lower(sD) -= X X^T + Y Y^T (n x n blocks, row-major; X or Y may be null).
 __device__ void cta_syrk_sub(double *sD, const double *X, const double *Y, int n) {
   const int ne = n * (n + 1) / 2;
@@ -78,39 +60,6 @@ __device__ void cta_syrk_sub(double *sD, const double *X, const double *Y, int n
       for (int k = 0; k < n; ++k) acc = fma(-Y[i * n + k], Y[j * n + k], acc);
     sD[i * n + j] = acc;
   }
-}
-
-// In-place lower Cholesky of the n x n block sA (lower triangle read);
-// sInv[j] = 1 / L_jj. A pivot that is not positive and finite is replaced by
-// 1 (so the launch finishes without NaNs) and the first such column + 1 is
-// returned; 0 on success.
-__device__ int cta_chol(double *sA, double *sInv, int n, int *sflag) {
-  if (threadIdx.x == 0) *sflag = 0;
-  for (int j = 0; j < n; ++j) {
-    if (threadIdx.x == 0) {
-      double d = sA[j * n + j];
-      if (!(d > 0.0) || !(d < INFINITY)) {
-        if (*sflag == 0) *sflag = j + 1;
-        d = 1.0;
-      }
-      const double r = rsqrt(d);
-      sA[j * n + j] = d * r;
-      sInv[j] = r;
-    }
-    __syncthreads();
-    const double r = sInv[j];
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) sA[i * n + j] *= r;
-    __syncthreads();
-    const int m = n - j - 1, ne = m * (m + 1) / 2;
-    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-      int a, b;
-      tri_ij(e, a, b);
-      const int i = j + 1 + a, k = j + 1 + b;
-      sA[i * n + k] = fma(-sA[i * n + j], sA[k * n + j], sA[i * n + k]);
-    }
-    __syncthreads();
-  }
-  return *sflag;
 }
 
 // X (m x n, row stride n) := X L^{-T}, L lower n x n with inverse diagonal inv.
@@ -276,26 +225,18 @@ constexpr double kRootEngage = 16.0;
 //  mode 2: the root after that refinement; returns at once unless *on.
 __global__ void __launch_bounds__(256) k_factor_root(F64View v, int mode, int *on) {
   extern __shared__ double sm[];
-  __shared__ int sflag, last;
+  __shared__ int last;
   if (mode == 2 && *((volatile const int *)on) == 0) return;
   const int nr = v.nr, ne = nr * (nr + 1) / 2;
   const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (e < ne) {
-    int i, j;
-    tri_ij(e, i, j);
-    const double val = v.R[i * nr + j] - root_sum_warp(v.U, v.S, nr, i, j);
-    if ((threadIdx.x & 31) == 0) {
-      v.Rt[i * nr + j] = val;
-      v.Rt[j * nr + i] = val;
-    }
-  }
+  if (e < ne) root_entry(v.U, v.R, v.S, nr, e, v.Rt);
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) last = (atomicAdd(&v.tickets[0], 1u) == gridDim.x - 1);
   __syncthreads();
   if (!last) return;
   __threadfence();
-  double *sR = sm, *sInv = sm + nr * nr;
+  double *sR = sm;
   for (int k = threadIdx.x; k < nr * nr; k += blockDim.x) sR[k] = __ldcg(v.Rt + k);
   __syncthreads();
   bool engage = false;
@@ -308,13 +249,7 @@ __global__ void __launch_bounds__(256) k_factor_root(F64View v, int mode, int *o
     }
   }
   __syncthreads();
-  const int fail = cta_chol(sR, sInv, nr, &sflag);
-  if (mode == 1 && fail) engage = true;
-  if (threadIdx.x == 0) {
-    if (mode == 1) *on = engage ? 1 : 0;
-    if (fail && !engage) report_not_spd(v.status, -1, 0);
-  }
-  cta_store_lower(v.LR, sR, nr);
+  root_chol_store(sR, nr, v.LR, v.status, mode == 1 ? &engage : nullptr, on);
   if (threadIdx.x == 0) v.tickets[0] = 0u;
 }
 
@@ -548,12 +483,15 @@ cudaError_t f64_prepare(int nb, int nr) {
 // other nb runs the runtime-size kernels above.
 void f64_launch_factor(const F64View &v, cudaStream_t st) {
   if (tail_nb_supported(v.nb)) {
-    TailView<double> t;
+    // the top kernel's last CTA finishes with the root step
+    TailView<double> t{};
     t.S = v.S; t.N = v.N; t.nb = v.nb; t.nr = v.nr; t.Lc = v.Lc;
     t.D = v.D; t.E = v.E; t.C = v.C; t.R = v.R;
     t.Ld = v.Ld; t.Ll = v.Ll; t.Lr = v.Lr; t.Dt = v.Dt; t.W = v.W; t.invd = v.invd;
     t.F = v.F; t.U = v.U; t.status = v.status;
+    t.Rt = v.Rt; t.LR = v.LR; t.tickets = v.tickets;
     tail_factor_launch<double>(t, st);
+    return;
   } else {
     const int T = factor_threads(v.nb);
     const size_t smem = f64_factor_smem(v.nb, v.nr);

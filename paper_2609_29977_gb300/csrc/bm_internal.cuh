@@ -144,6 +144,10 @@ struct TailView {
   T *invd;           // [S][N][nb]
   double *F, *U;     // [S][nr*nb], [S][nr*nr]
   Status *status;
+  // FP64 path: the top kernel's last CTA also forms R~ (Rt) and L_R (LR)
+  // when LR is set (ticket tickets[0]); null elsewhere
+  double *Rt, *LR;
+  unsigned *tickets;
 };
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }

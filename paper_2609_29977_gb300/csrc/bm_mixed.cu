@@ -363,7 +363,7 @@ void coupling_launch(const cx::CxView &v, int nb, int *mark, cudaStream_t st);
 void mixed_launch_factor(MixedState *m, const double *D, const double *E, const double *C, const double *R,
                          cudaStream_t st) {
   m->D = D; m->E = E; m->C = C; m->R = R;
-  TailView<float> t;
+  TailView<float> t{};
   t.S = m->S; t.N = m->N; t.nb = m->nb; t.nr = m->nr; t.Lc = m->Lc;
   t.D = D; t.E = E; t.C = C; t.R = R;
   t.Ld = m->Ld; t.Ll = m->Ll; t.Lr = m->Lr; t.Dt = m->Dt; t.W = m->W; t.invd = m->invd;

@@ -21,6 +21,7 @@
 // in parallel; bm_tail_factor.cu dispatches on the block size.
 #pragma once
 
+#include "bm_root.cuh"
 #include "bm_team.cuh"
 
 namespace bm {
@@ -226,6 +227,21 @@ __global__ void __launch_bounds__(512) k_factor_top(TailView<T> v, int lvl0) {
     __syncthreads();
   }
   if (tm.id == 0) x1_task<T, NB, TEAM>(v, tm, smem_raw, s);
+  if constexpr (sizeof(T) == sizeof(double)) {
+    if (v.LR) {
+      // the last tail to finish its U_i does the root step (Alg. 1 steps 4-5)
+      __shared__ int last;
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) last = atomicAdd(&v.tickets[0], 1u) == gridDim.x - 1;
+      __syncthreads();
+      if (last) {
+        __threadfence();
+        root_reduce_chol(v.U, v.R, v.S, v.nr, v.Rt, v.LR, v.status, (double *)smem_raw);
+        if (threadIdx.x == 0) v.tickets[0] = 0u;
+      }
+    }
+  }
   pdl_trigger();
 }
 
@@ -258,7 +274,9 @@ void launch_top(const TailView<T> &v, int lvl0, cudaStream_t st) {
   const size_t x1b = x1_bytes<T, NB>(v.nr);
   int tpc = TEAM >= 128 ? 4 : 512 / TEAM > 4 ? 4 : 512 / TEAM;
   while (tpc > 1 && per * tpc > 200 * 1024) tpc >>= 1;
-  const size_t smem = per * tpc > x1b ? per * tpc : x1b;
+  size_t smem = per * tpc > x1b ? per * tpc : x1b;
+  const size_t rootb = ((size_t)v.nr * v.nr + v.nr) * sizeof(double);
+  if (v.LR && rootb > smem) smem = rootb;
   launch_pdl(k_factor_top<T, NB, TEAM>, (unsigned)v.S, TEAM * tpc, smem, st, v, lvl0);
 }
 

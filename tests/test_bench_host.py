@@ -95,8 +95,10 @@ def test_derived_alu_peaks():
 
 def test_factor_kernel_names_match_the_launch_counts():
     from paper_2609_29977_gb300 import bm as core
-    # medium FP64: 4 level launches + top + root = the factor part of the 9 launches
-    assert bench._factor_kernels(64, 12, "fp64") == "k_factor_level_team x4 + k_factor_top + k_factor_root"
-    assert core.launches_per_step(64, 64, 12, 4) - 3 == 4 + 2
-    assert bench._factor_kernels(256, 48, "fp32ir") == "k_level_rows_w x6 + k_top_rows_w + k_factor_root"
+    # medium FP64: 4 level launches + top (whose last CTA does the root step)
+    # = the factor part of the 8 launches
+    assert bench._factor_kernels(64, 12, "fp64") == \
+        "k_factor_level_team x4 + k_factor_top (its last CTA does the root step)"
+    assert core.launches_per_step(64, 64, 12, 4) - 3 == 4 + 1
+    assert bench._factor_kernels(256, 48, "fp32ir").startswith("k_level_rows_w x6 + k_top_rows_w + k_pivot_spread")
     assert bench._factor_kernels(9, 5, "fp64") == "k_factor_level x4 + k_factor_x1 + k_factor_root"

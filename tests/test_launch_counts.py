@@ -1,7 +1,7 @@
 """The kernel counts the bench reports (``gpu_launches``), checked on CPU
 against counts taken by hand from the launch sequence of the library:
-factor = one launch per level below the top level, one top launch, one
-root launch; FP64 solve = forward, root, backward; mixed factor = the tail
+factor = one launch per level below the top level, one top launch (FP64:
+its last CTA does the root step; mixed: a root launch follows); FP64 solve = forward, root, backward; mixed factor = the tail
 launches plus the root (FP32-based root), plus four coupling-column
 launches (always refined), plus a pivot-spread reduction and a probing root
 (automatic); mixed solve =
@@ -22,8 +22,9 @@ def test_levels_of_the_medium_workload():
 
 
 def test_fp64_counts():
-    # medium: 4 level launches + top + root, then forward + root + backward
-    assert core.launches_per_step(64, 64, 12, 4) == 9
+    # medium: 4 level launches + top (whose last CTA does the root), then
+    # forward + root + backward
+    assert core.launches_per_step(64, 64, 12, 4) == 8
     # a block size without compiled tail kernels (generic per-level path)
     Lc = core.chain_levels(9)
     assert Lc == 4
