@@ -16,7 +16,7 @@ namespace {
 using namespace cx;
 
 template <int NB>
-__global__ void __launch_bounds__(256) k_cx_bwd(CxView v, int pass, int CS, int *mark) {
+__global__ void __launch_bounds__(256, 2) k_cx_bwd(CxView v, int pass, int CS, int *mark) {
   __shared__ __align__(16) float scr[XCfg<NB>::TEAMS * XCfg<NB>::SCR];
   pdl_wait();
   if (engaged(v)) {
@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(256) k_cx_bwd(CxView v, int pass, int CS, int 
 }
 
 template <int NB>
-__global__ void __launch_bounds__(256) k_cx_fwd(CxView v, int CS) {
+__global__ void __launch_bounds__(256, 2) k_cx_fwd(CxView v, int CS) {
   __shared__ __align__(16) float scr[XCfg<NB>::TEAMS * XCfg<NB>::SCR];
   pdl_wait();
   if (engaged(v)) fwd_multi<NB>(v, blockIdx.x / CS, (int)mx::cluster_rank(), CS, scr);

@@ -203,16 +203,13 @@ __device__ __forceinline__ void fwd_multi(const CxView &v, int s, int crank, int
           if (ctz32(mm) == lvl - 1) pl = mm;
         }
       }
-      float lrow_l[NB], lrow_r[NB], ld[NB];
-      if (pl) mx::load_row<NB>(lrow_l, v.Lr + (sb + (N - pl)) * NB2 + ir * NB);
-      if (pr) mx::load_row<NB>(lrow_r, v.Ll + (sb + (N - pr)) * NB2 + ir * NB);
-      float inv = 0.0f;
-      if (elim) {
-        mx::load_row<NB>(ld, v.Ld + (sb + (N - q)) * NB2 + ir * NB);
-        inv = v.invd[(sb + (N - q)) * NB + ir];
-      }
+      const float inv = elim ? v.invd[(sb + (N - q)) * NB + ir] : 0.0f;
       const size_t row = ((sb + (N - q)) * NB + ir) * ldc;
       for (int c0 = 0; c0 < ldc; c0 += RC) {
+        // one register row at a time (the first one loaded ahead of the
+        // staging barrier), so that two CTAs fit on an SM
+        float l[NB];
+        if (pl) mx::load_row<NB>(l, v.Lr + (sb + (N - pl)) * NB2 + ir * NB);
         if (pl) stage_chunk<NB, TS>(s0, v.Yb + (sb + (N - pl)) * NB * ldc + c0, ldc, i);
         if (pr) stage_chunk<NB, TS>(s1, v.Yb + (sb + (N - pr)) * NB * ldc + c0, ldc, i);
         float z[RC];
@@ -221,11 +218,15 @@ __device__ __forceinline__ void fwd_multi(const CxView &v, int s, int crank, int
           z[0] = a.x; z[1] = a.y; z[2] = a.z; z[3] = a.w; z[4] = b.x; z[5] = b.y; z[6] = b.z; z[7] = b.w;
         }
         tm.sync();
-        if (pl) gather_chunk<NB>(z, lrow_l, s0);
-        if (pr) gather_chunk<NB>(z, lrow_r, s1);
+        if (pl) gather_chunk<NB>(z, l, s0);
+        if (pr) {
+          mx::load_row<NB>(l, v.Ll + (sb + (N - pr)) * NB2 + ir * NB);
+          gather_chunk<NB>(z, l, s1);
+        }
         float *dst = v.Zr;
         if (elim) {
-          diag_fwd<NB, TS>(z, ld, inv, i, tm, sx);
+          mx::load_row<NB>(l, v.Ld + (sb + (N - q)) * NB2 + ir * NB);
+          diag_fwd<NB, TS>(z, l, inv, i, tm, sx);
           dst = v.Yb;
         }
         if (i < NB) {
@@ -270,13 +271,13 @@ __device__ __forceinline__ void bwd_multi(const CxView &v, int s, int crank, int
         b = (q + h <= N - 1) ? q + h : N;
         if (q > h) a = q - h;
       }
-      float lc_b[NB], lc_a[NB], lcol[NB];
-      if (b) load_col<NB>(lc_b, v.Lr + (sb + (N - q)) * NB2, ir);
-      if (a) load_col<NB>(lc_a, v.Ll + (sb + (N - q)) * NB2, ir);
-      load_col<NB>(lcol, v.Ld + (sb + (N - q)) * NB2, ir);
       const float inv = v.invd[(sb + (N - q)) * NB + ir];
       const size_t row = ((sb + (N - q)) * NB + ir) * ldc;
       for (int c0 = 0; c0 < ldc; c0 += RC) {
+        // one register column at a time (the first one loaded ahead of the
+        // staging barrier), so that two CTAs fit on an SM
+        float l[NB];
+        if (b) load_col<NB>(l, v.Lr + (sb + (N - q)) * NB2, ir);
         if (b) stage_chunk<NB, TS>(s0, out + (sb + (N - b)) * NB * ldc + c0, ldc, i);
         if (a) stage_chunk<NB, TS>(s1, out + (sb + (N - a)) * NB * ldc + c0, ldc, i);
         float z[RC];
@@ -297,9 +298,13 @@ __device__ __forceinline__ void bwd_multi(const CxView &v, int s, int crank, int
           diag_fwd<NB, TS>(z, lrow, inv, i, tm, sx);
         }
         tm.sync();
-        if (b) gather_chunk<NB>(z, lc_b, s0);
-        if (a) gather_chunk<NB>(z, lc_a, s1);
-        diag_bwd<NB, TS>(z, lcol, inv, i, tm, sx);
+        if (b) gather_chunk<NB>(z, l, s0);
+        if (a) {
+          load_col<NB>(l, v.Ll + (sb + (N - q)) * NB2, ir);
+          gather_chunk<NB>(z, l, s1);
+        }
+        load_col<NB>(l, v.Ld + (sb + (N - q)) * NB2, ir);
+        diag_bwd<NB, TS>(z, l, inv, i, tm, sx);
         float x0[RC];
         if (pass == 1) {
           const float4 u = ld4cg(v.Xa + row + c0), w = ld4cg(v.Xa + row + c0 + 4);
