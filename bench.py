@@ -857,6 +857,7 @@ def run_gpu(args):
         "e2e": {"value": whole_job_gflops(world, fl["total"], 1, e2e_step), "unit": "GFLOP/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
         "gpu_launches": launches_per_step * args.steps,
+        "schedule": _schedule_of(solver, bm),
         "clocks": clocks,
         "wall_s_timed": wall,
     }
@@ -917,6 +918,15 @@ def run_gpu(args):
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+def _schedule_of(solver, bm):
+    """The FP64 factor's launch schedule (autotuned on the first factor), or
+    None for the mixed path."""
+    try:
+        return solver.schedule()
+    except bm.BMError:
+        return None
 
 
 def _coupling_flags(args):

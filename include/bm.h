@@ -82,6 +82,9 @@ typedef enum {
  */
 #define BM_FLAG_COUPLING_REFINE 2u /* always refine the coupling columns */
 #define BM_FLAG_COUPLING_FP32 4u   /* never: R~ from the FP32 tail factor alone */
+/* BM_PREC_FP64: keep the default launch schedule of the tail factor instead
+ * of autotuning it on the first bm_factor (see bm_schedule) */
+#define BM_FLAG_NO_TUNE 8u
 
 typedef struct {
   int S, N, nb, nr;   /* scenarios (the paper's M), horizon, stage block, root block */
@@ -156,6 +159,28 @@ bm_status bm_factor(bm_handle h, const double *D, const double *E, const double 
  * Errors: BM_ERR_INVALID_ARG, BM_ERR_NOT_FACTORED, BM_ERR_CUDA.
  */
 bm_status bm_solve(bm_handle h, const double *r, double *x, void *stream);
+
+/*
+ * Launch schedule of the FP64 factor (not in the paper; the factor's
+ * arithmetic does not depend on it): *top_level = the first odd-even level
+ * of Gamma_{N-1} handled by the per-tail kernel (one CTA per tail, the
+ * levels separated by block barriers; the levels before it run as grid-wide
+ * launches over all tails), team_per_level[l] (32 entries, may be NULL) =
+ * the lanes that process one chain position in the grid-wide launch of
+ * level l (0 from top_level on). The first bm_factor of a handle takes the
+ * schedule from the autotune cache (file $BM_AUTOTUNE_CACHE, else
+ * ~/.cache/branch_mpc_gb300_autotune.json; key: GPU name and S, N, nb, nr)
+ * or, if absent, times every compiled team size per level and top levels one
+ * below and above the default on its inputs (synchronizing the stream) and
+ * stores the fastest; with BM_FLAG_NO_TUNE or BM_FLAG_NO_GRAPH the default
+ * rule is kept (about two warps' worth of lanes per SM sub-partition per
+ * level; the first level with at most four positions per tail starts the
+ * per-tail kernel). *source: 1 from the cache, 0 tuned by this handle,
+ * -1 the default rule.
+ * Errors: BM_ERR_NOT_FACTORED before the first bm_factor; BM_ERR_INVALID_ARG
+ * for mixed-precision handles and block sizes without compiled tail kernels.
+ */
+bm_status bm_schedule(bm_handle h, int *top_level, int *team_per_level, int *source);
 
 /*
  * Synchronizes stream, then reports the sticky device status of the last

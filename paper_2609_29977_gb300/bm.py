@@ -18,6 +18,7 @@ BM_PREC_FP32_IR = 1
 BM_FLAG_NO_GRAPH = 1
 BM_FLAG_COUPLING_REFINE = 2   # mixed precision: always refine the coupling columns
 BM_FLAG_COUPLING_FP32 = 4     # mixed precision: never (root from the FP32 tail factor alone)
+BM_FLAG_NO_TUNE = 8           # FP64: keep the default launch schedule (no autotuning)
 
 BM_OK = 0
 STATUS_NAMES = {0: "BM_OK", 1: "BM_ERR_INVALID_ARG", 2: "BM_ERR_NOT_SPD", 3: "BM_ERR_OOM",
@@ -25,7 +26,7 @@ STATUS_NAMES = {0: "BM_OK", 1: "BM_ERR_INVALID_ARG", 2: "BM_ERR_NOT_SPD", 3: "BM
                 7: "BM_ERR_NOT_FACTORED"}
 
 EXPORTED_SYMBOLS = ("bm_version", "bm_status_string", "bm_workspace_bytes", "bm_analyze", "bm_factor",
-                    "bm_solve", "bm_query", "bm_export_factor", "bm_factor_solve_host", "bm_destroy",
+                    "bm_solve", "bm_query", "bm_schedule", "bm_export_factor", "bm_factor_solve_host", "bm_destroy",
                     "bm_factor_solve_noalloc", "bm_round_to_fp32", "bm_batch_workspace_bytes",
                     "bm_batch_analyze", "bm_batch_factor", "bm_batch_solve", "bm_batch_query",
                     "bm_batch_schedule", "bm_batch_destroy", "bm_server_request_bytes", "bm_server_create",
@@ -134,6 +135,9 @@ def _load():
     lib.bm_batch_solve.argtypes = [vp, vp, vp, vp]
     lib.bm_batch_query.restype = ctypes.c_int
     lib.bm_batch_query.argtypes = [vp, vp, ctypes.POINTER(bm_info)]
+    lib.bm_schedule.restype = ctypes.c_int
+    lib.bm_schedule.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_int)]
     lib.bm_batch_schedule.restype = ctypes.c_int
     lib.bm_batch_schedule.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int)]
@@ -286,6 +290,18 @@ def bm_query(h, stream=None) -> dict:
             "backward_error": info.backward_error, "coupling_refined": int(info.coupling_refined)}
 
 
+def bm_schedule(h) -> dict:
+    """The FP64 factor's launch schedule (see include/bm.h): top level of the
+    per-tail kernel, team size of each grid-wide level, and where it came
+    from ("cache", "tuned" or "rule")."""
+    top = ctypes.c_int()
+    teams = (ctypes.c_int * 32)()
+    src = ctypes.c_int()
+    _check(_load().bm_schedule(h, ctypes.byref(top), teams, ctypes.byref(src)), "bm_schedule")
+    return {"top_level": int(top.value), "teams": [int(teams[l]) for l in range(int(top.value))],
+            "source": {1: "cache", 0: "tuned", -1: "rule"}.get(int(src.value), str(src.value))}
+
+
 def bm_export_factor(h, Ld=None, Ll=None, Lr=None, F=None, LR=None, stream=None) -> None:
     _check(_load().bm_export_factor(h, _ptr(Ld, "Ld"), _ptr(Ll, "Ll"), _ptr(Lr, "Lr"), _ptr(F, "F"),
                                     _ptr(LR, "LR"), _stream(stream)), "bm_export_factor")
@@ -349,6 +365,9 @@ class BranchKKTSolver:
 
     def query(self, stream=None) -> dict:
         return bm_query(self.h, stream)
+
+    def schedule(self) -> dict:
+        return bm_schedule(self.h)
 
     def export_factor(self, stream=None) -> dict:
         import torch

@@ -5,17 +5,23 @@
 // entry.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <new>
+#include <string>
 #include <type_traits>
+#include <vector>
 
 #include "bm_internal.cuh"
 
 namespace bm {
 size_t f64_factor_smem(int nb, int nr);
 cudaError_t f64_prepare(int nb, int nr);
-void f64_launch_factor(const F64View &v, cudaStream_t st);
+void f64_launch_factor(const F64View &v, cudaStream_t st, const TailSched *sc = nullptr);
+bool f64_tune(const F64View &v, cudaStream_t st, TailSched *out);
+bool tune_cache_lookup(const std::string &key, std::vector<int> &vals);
+void tune_cache_store(const std::string &key, const std::vector<int> &vals);
 void f64_launch_solve(const F64View &v, const double *r, double *x, double *r0t, cudaStream_t st);
 
 // mixed precision path (bm_mixed.cu)
@@ -60,6 +66,11 @@ struct bm_handle_s {
   bool loop_pdl = true;            // programmatic launches inside that body (cleared if they do not instantiate)
   GraphSlot gfac, gsol;
   bool factored = false;
+  // FP64 tail factor's launch schedule: -1 = the default rule (not tuned),
+  // 0 = tuned on this handle's first factor, 1 = taken from the tune cache
+  TailSched sched{};
+  int sched_src = -1;
+  bool sched_ready = false;
   // host-entry staging (allocated on first use)
   double *sD = nullptr, *sE = nullptr, *sC = nullptr, *sR = nullptr, *sr = nullptr, *sx = nullptr;
 };
@@ -282,6 +293,41 @@ static bm_status run(bm_handle h, GraphSlot &slot, const void *const *key, int n
   return cudaGraphLaunch(slot.exec, st) == cudaSuccess ? BM_OK : BM_ERR_CUDA;
 }
 
+// The FP64 factor's launch schedule, once per handle: from the tune cache
+// (keyed by GPU and system shape), else tuned on these inputs (the stream
+// is synchronized; the tuning runs are full factors, overwritten by the
+// factor that follows), unless BM_FLAG_NO_TUNE or BM_FLAG_NO_GRAPH asks for
+// the default rule.
+static void prepare_schedule(bm_handle h, const F64View &v, cudaStream_t st) {
+  const bm_desc &d = h->desc;
+  tail_default_schedule(d.S, d.N, d.nb, &h->sched);
+  h->sched_src = -1;
+  h->sched_ready = true;
+  if ((d.flags & (BM_FLAG_NO_TUNE | BM_FLAG_NO_GRAPH)) || !tail_nb_supported(d.nb)) return;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, h->device) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  char kb[320];
+  snprintf(kb, sizeof kb, "fp64-schedule|%.200s|S=%d|N=%d|nb=%d|nr=%d", prop.name, d.S, d.N, d.nb, d.nr);
+  std::vector<int> vals;
+  if (tune_cache_lookup(kb, vals) && (int)vals.size() == 1 + (vals.empty() ? 0 : vals[0]) && vals[0] >= 0 &&
+      vals[0] <= h->Lc && vals[0] < 32) {
+    h->sched.top = vals[0];
+    for (int l = 0; l < 32; ++l) h->sched.team[l] = l < vals[0] ? vals[1 + l] : 0;
+    h->sched_src = 1;
+    return;
+  }
+  TailSched t;
+  if (!f64_tune(v, st, &t)) return;
+  h->sched = t;
+  h->sched_src = 0;
+  vals.assign(1, t.top);
+  for (int l = 0; l < t.top; ++l) vals.push_back(t.team[l]);
+  tune_cache_store(kb, vals);
+}
+
 extern "C" bm_status bm_factor(bm_handle h, const double *D, const double *E, const double *C,
                                const double *R, void *stream) {
   if (!h || !D || !C || !R || (h->desc.N > 1 && !E)) return BM_ERR_INVALID_ARG;
@@ -299,9 +345,11 @@ extern "C" bm_status bm_factor(bm_handle h, const double *D, const double *E, co
   } else {
     F64View v = h->v;
     v.D = D; v.E = E; v.C = C; v.R = R;
+    if (!h->sched_ready) prepare_schedule(h, v, st);
+    const TailSched *sc = &h->sched;
     s = run(h, h->gfac, key, 4, st, [&](cudaStream_t cs, bool) {
       cudaMemsetAsync(v.status, 0, sizeof(Status), cs);
-      f64_launch_factor(v, cs);
+      f64_launch_factor(v, cs, sc);
     });
     h->v.D = D; h->v.E = E; h->v.C = C; h->v.R = R;
   }
@@ -337,6 +385,17 @@ extern "C" bm_status bm_solve(bm_handle h, const double *r, double *x, void *str
   double *r0t = h->r0t;
   const void *key[2] = {r, x};
   return run(h, h->gsol, key, 2, st, [&](cudaStream_t cs, bool) { f64_launch_solve(v, r, x, r0t, cs); });
+}
+
+extern "C" bm_status bm_schedule(bm_handle h, int *top_level, int *team_per_level, int *source) {
+  if (!h) return BM_ERR_INVALID_ARG;
+  if (h->mixed || !tail_nb_supported(h->desc.nb)) return BM_ERR_INVALID_ARG;
+  if (!h->sched_ready) return BM_ERR_NOT_FACTORED;
+  if (top_level) *top_level = h->sched.top;
+  if (team_per_level)
+    for (int l = 0; l < 32; ++l) team_per_level[l] = l < h->sched.top ? h->sched.team[l] : 0;
+  if (source) *source = h->sched_src;
+  return BM_OK;
 }
 
 extern "C" bm_status bm_query(bm_handle h, void *stream, bm_info *info) {

@@ -41,6 +41,8 @@
 #include "bm_tail_rows.cuh"
 
 namespace bm {
+bool tune_cache_lookup(const std::string &key, std::vector<int> &vals);
+void tune_cache_store(const std::string &key, const std::vector<int> &vals);
 
 size_t mixed_bytes(int S, int N, int nb, int nr);
 
@@ -321,65 +323,16 @@ bool batch_nb_ok(int nb) {
   return false;
 }
 
-// ---- autotune cache (a flat JSON object: "key": [threads, ctas_per_sm]) ----
-
-std::mutex g_tune_mutex;
-
-std::string cache_path() {
-  const char *p = getenv("BM_AUTOTUNE_CACHE");
-  if (p && *p) return p;
-  const char *home = getenv("HOME");
-  return std::string(home && *home ? home : "/tmp") + "/.cache/branch_mpc_gb300_autotune.json";
-}
-
+// The autotune cache (bm_tune.cu) keeps [threads, ctas_per_sm] per batch signature.
 bool cache_lookup(const std::string &key, int *threads, int *cps) {
-  std::lock_guard<std::mutex> lk(g_tune_mutex);
-  FILE *f = fopen(cache_path().c_str(), "r");
-  if (!f) return false;
-  std::string s;
-  char buf[4096];
-  size_t n;
-  while ((n = fread(buf, 1, sizeof buf, f)) > 0) s.append(buf, n);
-  fclose(f);
-  const std::string needle = "\"" + key + "\": [";
-  const size_t p = s.find(needle);
-  if (p == std::string::npos) return false;
-  return sscanf(s.c_str() + p + needle.size(), "%d, %d", threads, cps) == 2;
+  std::vector<int> v;
+  if (!tune_cache_lookup(key, v) || v.size() != 2) return false;
+  *threads = v[0];
+  *cps = v[1];
+  return true;
 }
 
-void cache_store(const std::string &key, int threads, int cps) {
-  std::lock_guard<std::mutex> lk(g_tune_mutex);
-  const std::string path = cache_path();
-  std::string s;
-  if (FILE *f = fopen(path.c_str(), "r")) {
-    char buf[4096];
-    size_t n;
-    while ((n = fread(buf, 1, sizeof buf, f)) > 0) s.append(buf, n);
-    fclose(f);
-  }
-  std::vector<std::string> entries;
-  size_t p = 0;
-  while ((p = s.find('"', p)) != std::string::npos) {
-    const size_t q = s.find('"', p + 1);
-    const size_t e = s.find(']', q);
-    if (q == std::string::npos || e == std::string::npos) break;
-    const std::string k = s.substr(p + 1, q - p - 1);
-    if (k != key) entries.push_back(s.substr(p, e - p + 1));
-    p = e + 1;
-  }
-  char mine[512];
-  snprintf(mine, sizeof mine, "\"%s\": [%d, %d]", key.c_str(), threads, cps);
-  entries.push_back(mine);
-  const std::string dir = path.substr(0, path.find_last_of('/'));
-  for (size_t i = 1; i <= dir.size(); ++i)   // create missing directories (best effort)
-    if (i == dir.size() || dir[i] == '/') mkdir(dir.substr(0, i).c_str(), 0755);
-  FILE *f = fopen(path.c_str(), "w");
-  if (!f) return;
-  fputs("{\n", f);
-  for (size_t i = 0; i < entries.size(); ++i) fprintf(f, "  %s%s\n", entries[i].c_str(), i + 1 < entries.size() ? "," : "");
-  fputs("}\n", f);
-  fclose(f);
-}
+void cache_store(const std::string &key, int threads, int cps) { tune_cache_store(key, {threads, cps}); }
 
 // One lane waits with the batched factor's bounded wait on a counter that
 // nothing increments: the wait must give up after `limit` cycles and leave

@@ -481,16 +481,25 @@ cudaError_t f64_prepare(int nb, int nr) {
 
 // Block sizes with compile-time kernels (bm_tail_factor.cuh) use those; any
 // other nb runs the runtime-size kernels above.
-void f64_launch_factor(const F64View &v, cudaStream_t st) {
+static TailView<double> tail_view_of(const F64View &v) {
+  TailView<double> t{};
+  t.S = v.S; t.N = v.N; t.nb = v.nb; t.nr = v.nr; t.Lc = v.Lc;
+  t.D = v.D; t.E = v.E; t.C = v.C; t.R = v.R;
+  t.Ld = v.Ld; t.Ll = v.Ll; t.Lr = v.Lr; t.Dt = v.Dt; t.W = v.W; t.invd = v.invd;
+  t.F = v.F; t.U = v.U; t.status = v.status;
+  t.Rt = v.Rt; t.LR = v.LR; t.tickets = v.tickets;
+  return t;
+}
+
+// Tunes the tail factor's launch schedule on v's inputs (synchronizes st).
+bool f64_tune(const F64View &v, cudaStream_t st, TailSched *out) {
+  return tail_factor_tune(tail_view_of(v), st, out);
+}
+
+void f64_launch_factor(const F64View &v, cudaStream_t st, const TailSched *sc) {
   if (tail_nb_supported(v.nb)) {
     // the top kernel's last CTA finishes with the root step
-    TailView<double> t{};
-    t.S = v.S; t.N = v.N; t.nb = v.nb; t.nr = v.nr; t.Lc = v.Lc;
-    t.D = v.D; t.E = v.E; t.C = v.C; t.R = v.R;
-    t.Ld = v.Ld; t.Ll = v.Ll; t.Lr = v.Lr; t.Dt = v.Dt; t.W = v.W; t.invd = v.invd;
-    t.F = v.F; t.U = v.U; t.status = v.status;
-    t.Rt = v.Rt; t.LR = v.LR; t.tickets = v.tickets;
-    tail_factor_launch<double>(t, st);
+    tail_factor_launch<double>(tail_view_of(v), st, sc);
     return;
   } else {
     const int T = factor_threads(v.nb);

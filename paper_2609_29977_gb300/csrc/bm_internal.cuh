@@ -152,6 +152,14 @@ struct TailView {
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Launch schedule of the FP64 tail factor: the first level that the per-tail
+// top kernel takes over (one CTA per tail), and the team size (lanes per
+// chain position) of each grid-wide level launch before it.
+struct TailSched {
+  int top;
+  int team[32];
+};
+
 // Block sizes with compile-time tail kernels.
 #define BM_TAIL_NB_LIST(X) X(2) X(3) X(4) X(6) X(8) X(12) X(16) X(24) X(32) X(48)
 // Block sizes whose FP32 tails use the register-row kernels (bm_tail_rows.cuh).
@@ -170,8 +178,15 @@ inline int top_level(int N) {
 
 bool tail_nb_supported(int nb);
 cudaError_t tail_factor_prepare();
+// sc: schedule of the FP64 tail factor (null: the default rule); ev: if not
+// null, top + 2 events recorded before the first launch and after each one.
 template <typename T>
-void tail_factor_launch(const TailView<T> &v, cudaStream_t st);
+void tail_factor_launch(const TailView<T> &v, cudaStream_t st, const TailSched *sc = nullptr,
+                        cudaEvent_t *ev = nullptr);
+// The default schedule, and the autotuned one (times candidate team sizes
+// per level and top levels on the given inputs, synchronizing st).
+void tail_default_schedule(int S, int N, int nb, TailSched *sc);
+bool tail_factor_tune(const TailView<double> &v, cudaStream_t st, TailSched *best);
 
 // Launch with programmatic stream serialization (PDL): the kernel may begin
 // while its predecessor drains and waits in griddepcontrol.wait.

@@ -31,7 +31,7 @@
 namespace bm {
 size_t f64_factor_smem(int nb, int nr);
 cudaError_t f64_prepare(int nb, int nr);
-void f64_launch_factor(const F64View &v, cudaStream_t st);
+void f64_launch_factor(const F64View &v, cudaStream_t st, const TailSched *sc = nullptr);
 void f64_launch_solve(const F64View &v, const double *r, double *x, double *r0t, cudaStream_t st);
 }  // namespace bm
 

@@ -313,21 +313,24 @@ void launch_level_clamped(const TailView<T> &v, int lvl, long tasks, cudaStream_
 }
 
 template <typename T, int NB>
-void launch_tail_nb(const TailView<T> &v, cudaStream_t st) {
-  const int Tl = top_level(v.N);
+void launch_tail_nb(const TailView<T> &v, cudaStream_t st, const TailSched *sc, cudaEvent_t *ev) {
+  const int Tl = sc ? sc->top : top_level(v.N);
+  if (ev) cudaEventRecord(ev[0], st);
   for (int l = 0; l < Tl; ++l) {
     const int E = level_elims(v.N, l);
     const int G = l == 0 ? 0 : ((v.N - 1) >> (l + 1)) + 1;
     const long tasks = (long)v.S * (E + G);
-    switch (pick_team(tasks, NB)) {
+    switch (sc ? sc->team[l] : pick_team(tasks, NB)) {
       case 8: launch_level_clamped<T, NB, 8>(v, l, tasks, st); break;
       case 16: launch_level_clamped<T, NB, 16>(v, l, tasks, st); break;
       case 32: launch_level_clamped<T, NB, 32>(v, l, tasks, st); break;
       case 64: launch_level_clamped<T, NB, 64>(v, l, tasks, st); break;
       default: launch_level_clamped<T, NB, 128>(v, l, tasks, st); break;
     }
+    if (ev) cudaEventRecord(ev[l + 1], st);
   }
   launch_top<T, NB, team_top(NB)>(v, Tl, st);
+  if (ev) cudaEventRecord(ev[Tl + 1], st);
 }
 
 }  // namespace tail

@@ -4,15 +4,15 @@
 
 namespace bm {
 namespace tail {
-template void launch_tail_nb<float, 2>(const TailView<float> &, cudaStream_t);
+template void launch_tail_nb<float, 2>(const TailView<float> &, cudaStream_t, const TailSched *, cudaEvent_t *);
 template cudaError_t prepare_nb<float, 2>();
-template void launch_tail_nb<float, 3>(const TailView<float> &, cudaStream_t);
+template void launch_tail_nb<float, 3>(const TailView<float> &, cudaStream_t, const TailSched *, cudaEvent_t *);
 template cudaError_t prepare_nb<float, 3>();
-template void launch_tail_nb<float, 4>(const TailView<float> &, cudaStream_t);
+template void launch_tail_nb<float, 4>(const TailView<float> &, cudaStream_t, const TailSched *, cudaEvent_t *);
 template cudaError_t prepare_nb<float, 4>();
-template void launch_tail_nb<float, 6>(const TailView<float> &, cudaStream_t);
+template void launch_tail_nb<float, 6>(const TailView<float> &, cudaStream_t, const TailSched *, cudaEvent_t *);
 template cudaError_t prepare_nb<float, 6>();
-template void launch_tail_nb<float, 8>(const TailView<float> &, cudaStream_t);
+template void launch_tail_nb<float, 8>(const TailView<float> &, cudaStream_t, const TailSched *, cudaEvent_t *);
 template cudaError_t prepare_nb<float, 8>();
 }  // namespace tail
 template void rows::launch_tail_rows<float, 2>(const TailView<float> &, cudaStream_t);

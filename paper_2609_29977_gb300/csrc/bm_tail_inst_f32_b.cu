@@ -4,9 +4,9 @@
 
 namespace bm {
 namespace tail {
-template void launch_tail_nb<float, 12>(const TailView<float> &, cudaStream_t);
+template void launch_tail_nb<float, 12>(const TailView<float> &, cudaStream_t, const TailSched *, cudaEvent_t *);
 template cudaError_t prepare_nb<float, 12>();
-template void launch_tail_nb<float, 16>(const TailView<float> &, cudaStream_t);
+template void launch_tail_nb<float, 16>(const TailView<float> &, cudaStream_t, const TailSched *, cudaEvent_t *);
 template cudaError_t prepare_nb<float, 16>();
 }  // namespace tail
 template void rows::launch_tail_rows<float, 12>(const TailView<float> &, cudaStream_t);

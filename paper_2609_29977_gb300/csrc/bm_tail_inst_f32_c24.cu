@@ -4,7 +4,7 @@
 
 namespace bm {
 namespace tail {
-template void launch_tail_nb<float, 24>(const TailView<float> &, cudaStream_t);
+template void launch_tail_nb<float, 24>(const TailView<float> &, cudaStream_t, const TailSched *, cudaEvent_t *);
 template cudaError_t prepare_nb<float, 24>();
 }  // namespace tail
 template void rows::launch_tail_rows<float, 24>(const TailView<float> &, cudaStream_t);

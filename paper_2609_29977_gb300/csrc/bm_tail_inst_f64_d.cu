@@ -3,7 +3,7 @@
 
 namespace bm {
 namespace tail {
-template void launch_tail_nb<double, 48>(const TailView<double> &, cudaStream_t);
+template void launch_tail_nb<double, 48>(const TailView<double> &, cudaStream_t, const TailSched *, cudaEvent_t *);
 template cudaError_t prepare_nb<double, 48>();
 }  // namespace tail
 }  // namespace bm

@@ -307,3 +307,35 @@ def test_fp64_handles_with_different_block_sizes_coexist():
     check_solution(big, x)
     h_small.close()
     h_big.close()
+
+
+def test_fp64_schedule_is_tuned_cached_and_does_not_change_the_bits(tmp_path, monkeypatch):
+    """The first factor of a handle tunes the launch schedule (team size per
+    grid-wide level, top level of the per-tail kernel) and stores it; a second
+    handle of the same shape takes it from the cache. Every element of every
+    block is computed by one thread in a fixed order whatever the schedule,
+    so the tuned, cached and default schedules give the same bits."""
+    monkeypatch.setenv("BM_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    bm = _bm()
+    S, N, nb, nr = 16, 40, 12, 4
+    d = gen(S, N, nb, nr, seed=3, barrier=(-3, 3))
+    g = to_dev(d)
+    outs = []
+    for flags in (0, 0, bm.BM_FLAG_NO_TUNE):
+        solver = bm.BranchKKTSolver(S, N, nb, nr, flags=flags)
+        solver.factor(g["D"], g["E"], g["C"], g["R"])
+        x = solver.solve(g["r"]).cpu().numpy()
+        outs.append((x, solver.schedule(), solver.query()))
+        solver.close()
+    (x1, s1, i1), (x2, s2, i2), (x3, s3, i3) = outs
+    assert s1["source"] == "tuned" and s2["source"] == "cache" and s3["source"] == "rule", (s1, s2, s3)
+    assert s1["top_level"] == s2["top_level"] and s1["teams"] == s2["teams"]
+    assert 0 <= s1["top_level"] <= 6 and all(t in (8, 16, 32, 64) for t in s1["teams"]), s1
+    assert i1["status"] == i2["status"] == i3["status"] == 0
+    assert np.array_equal(x1, x2) and np.array_equal(x1, x3)
+    assert "fp64-schedule" in (tmp_path / "tune.json").read_text()
+    # mixed-precision handles have no tunable schedule
+    mixed = bm.BranchKKTSolver(S, N, nb, nr, precision=bm.BM_PREC_FP32_IR)
+    with pytest.raises(bm.BMError):
+        mixed.schedule()
+    mixed.close()
