@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(256, 2) k_cx_fwd(CxView v, int CS) {
 }
 
 template <int NB>
-__global__ void __launch_bounds__(256) k_cx_residual(CxView v) {
+__global__ void __launch_bounds__(256, 4) k_cx_residual(CxView v) {
   pdl_wait();
   if (engaged(v)) {
     const long nrow = (long)v.S * v.N * NB;

@@ -314,7 +314,7 @@ namespace rows {
 // Grid-wide level with register rows: tasks of all tails, eliminated
 // positions first; TS lanes per task, 128 threads per CTA.
 template <typename T, int NB>
-__global__ void __launch_bounds__(128) k_level_rows(TailView<T> v, int lvl) {
+__global__ void __launch_bounds__(128, 4) k_level_rows(TailView<T> v, int lvl) {
   constexpr int TS = Cfg<NB>::TS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int team = threadIdx.x / TS, lane = threadIdx.x % TS;
