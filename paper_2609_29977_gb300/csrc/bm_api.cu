@@ -23,6 +23,7 @@ bool f64_tune(const F64View &v, cudaStream_t st, TailSched *out);
 bool tune_cache_lookup(const std::string &key, std::vector<int> &vals);
 void tune_cache_store(const std::string &key, const std::vector<int> &vals);
 void f64_launch_solve(const F64View &v, const double *r, double *x, double *r0t, cudaStream_t st);
+void f64_launch_export_ld(const F64View &v, double *Ld, cudaStream_t st);
 
 // mixed precision path (bm_mixed.cu)
 struct MixedState;
@@ -432,7 +433,10 @@ extern "C" bm_status bm_export_factor(bm_handle h, double *Ld, double *Ll, doubl
   const F64View &v = h->v;
   const size_t bb = (size_t)v.S * v.N * v.nb * v.nb * sizeof(double);
   cudaError_t e = cudaSuccess;
-  if (Ld && e == cudaSuccess) e = cudaMemcpyAsync(Ld, v.Ld, bb, cudaMemcpyDeviceToDevice, st);
+  if (Ld && e == cudaSuccess) {
+    f64_launch_export_ld(v, Ld, st);
+    e = cudaGetLastError();
+  }
   if (Ll && e == cudaSuccess) e = cudaMemcpyAsync(Ll, v.Ll, bb, cudaMemcpyDeviceToDevice, st);
   if (Lr && e == cudaSuccess) e = cudaMemcpyAsync(Lr, v.Lr, bb, cudaMemcpyDeviceToDevice, st);
   if (F && e == cudaSuccess)

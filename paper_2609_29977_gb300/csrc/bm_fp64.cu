@@ -531,6 +531,23 @@ void f64_launch_factor_root_raw(int S, int nr, const double *U, const double *R,
   k_factor_root<<<(ne + 7) / 8, 256, ((size_t)nr * nr + nr) * sizeof(double), st>>>(v, mode, on);
 }
 
+// Lower triangles of nblk nb x nb blocks, upper triangles zero (the tail
+// factor keeps the scaled unit factor's transpose above the diagonal).
+__global__ void k_copy_lower(const double *__restrict__ src, double *__restrict__ dst, long n, int nb) {
+  const int nb2 = nb * nb;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+    const int w = (int)(e % nb2), i = w / nb, j = w - i * nb;
+    dst[e] = j <= i ? src[e] : 0.0;
+  }
+}
+
+void f64_launch_export_ld(const F64View &v, double *Ld, cudaStream_t st) {
+  const long n = (long)v.S * v.N * v.nb * v.nb;
+  long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_copy_lower<<<(unsigned)blocks, 256, 0, st>>>(v.Ld, Ld, n, v.nb);
+}
+
 void f64_launch_solve_root(const F64View &v, const double *r, double *x, double *r0t, cudaStream_t st) {
   k_solve_root<<<v.nr, 256, 0, st>>>(v, r, x, r0t);
 }

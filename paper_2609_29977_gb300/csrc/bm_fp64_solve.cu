@@ -34,12 +34,20 @@ struct SolveCfg {
   static constexpr int TS = NB <= 4 ? 4 : NB <= 8 ? 8 : NB <= 16 ? 16 : NB <= 32 ? 32 : 64;
   static constexpr int THREADS = 256;
   static constexpr int TEAMS = THREADS / TS;
+  // CTAs per SM that the register-capped instantiation must allow: with
+  // one CTA per tail, four per SM keep up to 608 tails in a single wave on
+  // 152 SMs (the uncapped one, 80 registers at nb = 24, fits three)
+  static constexpr int MINB = NB <= 32 ? 4 : 2;
 };
+
+// Whether a launch of S * CS CTAs needs the register-capped kernels: more
+// CTAs than three per SM would otherwise run in a second, mostly empty wave.
+inline bool solve_capped(int S, int CS) { return (long)S * CS > 3 * 152; }
 
 // Forward levels of one tail, then x_1: y_1 = L_{i,1}^{-1} z_1 and
 // t_i = F_{i,1} y_1. Grid: S * CS CTAs, clusters of CS.
-template <int NB>
-__global__ void __launch_bounds__(256) k_solve_fwd_tail(F64View v, const double *__restrict__ r, int CS) {
+template <int NB, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_solve_fwd_tail(F64View v, const double *__restrict__ r, int CS) {
   constexpr int TS = SolveCfg<NB>::TS, TEAMS = SolveCfg<NB>::TEAMS, NB2 = NB * NB;
   __shared__ double sY[TEAMS][NB];
   const Team<TS> tm;
@@ -93,32 +101,31 @@ __global__ void __launch_bounds__(256) k_solve_fwd_tail(F64View v, const double 
         if (i < NB) v.zt[zoff + i] = z;
         continue;
       }
-      // y = L_qq^{-1} z, row i of L_qq held in registers
-      double Lrow[NB];
-      const double *Ld = v.Ld + (sb + (N - q)) * NB2 + (i < NB ? i : 0) * NB;
-#pragma unroll
-      for (int k = 0; k < NB; ++k) Lrow[k] = Ld[k];
+      // y = L_qq^{-1} z as M w = z, y = inv .* w with the unit lower
+      // factor M = L_qq diag(L_qq)^-1, whose row i is column i of the
+      // stored block's upper triangle (read coalesced across the lanes)
+      const double *Mrow = v.Ld + (sb + (N - q)) * NB2 + (i < NB ? i : 0);
       const double inv = i < NB ? v.invd[zoff + i] : 0.0;
       if (TS <= 32) {
         const int base = (threadIdx.x & 31) & ~(TS - 1);
 #pragma unroll
-        for (int j = 0; j < NB; ++j) {
-          if (i == j) z *= inv;
-          const double yj = __shfl_sync(tm.mask, z, base + j);
-          if (i > j && i < NB) z = fma(-Lrow[j], yj, z);
+        for (int j = 0; j < NB - 1; ++j) {
+          const double wj = __shfl_sync(tm.mask, z, base + j);
+          if (i > j && i < NB) z = fma(-Mrow[j * NB], wj, z);
         }
+        z *= inv;
         if (i < NB) sY[tm.id][i] = z;
         tm.sync();
       } else {
 #pragma unroll
-        for (int j = 0; j < NB; ++j) {
-          if (i == j) {
-            z *= inv;
-            sY[tm.id][j] = z;
-          }
+        for (int j = 0; j < NB - 1; ++j) {
+          if (i == j) sY[tm.id][j] = z;
           tm.sync();
-          if (i > j && i < NB) z = fma(-Lrow[j], sY[tm.id][j], z);
+          if (i > j && i < NB) z = fma(-Mrow[j * NB], sY[tm.id][j], z);
         }
+        z *= inv;
+        tm.sync();
+        if (i < NB) sY[tm.id][i] = z;
       }
       if (i < NB) v.y[zoff + i] = z;
       if (last) {
@@ -141,8 +148,8 @@ __global__ void __launch_bounds__(256) k_solve_fwd_tail(F64View v, const double 
 // Backward: root propagation y_1 -= F_{i,1}^T x_0, x_1 = L_{i,1}^{-T} y_1,
 // then levels Lc-1..0: x_q = L_qq^{-T}(y_q - L_{a,q}^T x_a - L_{b,q}^T x_b),
 // written in natural order.
-template <int NB>
-__global__ void __launch_bounds__(256) k_solve_bwd_tail(F64View v, double *__restrict__ x, int CS) {
+template <int NB, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_solve_bwd_tail(F64View v, double *__restrict__ x, int CS) {
   constexpr int TS = SolveCfg<NB>::TS, TEAMS = SolveCfg<NB>::TEAMS, NB2 = NB * NB;
   __shared__ double sX[TEAMS][NB];
   const Team<TS> tm;
@@ -180,29 +187,28 @@ __global__ void __launch_bounds__(256) k_solve_bwd_tail(F64View v, double *__res
           }
         }
       }
-      // x = L_qq^{-T} z, column i of L_qq held in registers
-      double Lcol[NB];
-      const double *Ld = v.Ld + (sb + (N - q)) * NB2 + (i < NB ? i : 0);
+      // x = L_qq^{-T} z as M^T x = inv .* z with the unit lower factor
+      // M = L_qq diag(L_qq)^-1, whose column i is row i of the stored
+      // block's upper triangle
+      double Mcol[NB];
+      const double *Ld = v.Ld + (sb + (N - q)) * NB2 + (i < NB ? i : 0) * NB;
 #pragma unroll
-      for (int k = 0; k < NB; ++k) Lcol[k] = Ld[k * NB];
+      for (int k = 0; k < NB; ++k) Mcol[k] = Ld[k];
       const double inv = i < NB ? v.invd[zoff + i] : 0.0;
+      z *= inv;
       if (TS <= 32) {
         const int base = (threadIdx.x & 31) & ~(TS - 1);
 #pragma unroll
-        for (int j = NB - 1; j >= 0; --j) {
-          if (i == j) z *= inv;
+        for (int j = NB - 1; j > 0; --j) {
           const double xj = __shfl_sync(tm.mask, z, base + j);
-          if (i < j) z = fma(-Lcol[j], xj, z);
+          if (i < j) z = fma(-Mcol[j], xj, z);
         }
       } else {
 #pragma unroll
-        for (int j = NB - 1; j >= 0; --j) {
-          if (i == j) {
-            z *= inv;
-            sX[tm.id][j] = z;
-          }
+        for (int j = NB - 1; j > 0; --j) {
+          if (i == j) sX[tm.id][j] = z;
           tm.sync();
-          if (i < j) z = fma(-Lcol[j], sX[tm.id][j], z);
+          if (i < j) z = fma(-Mcol[j], sX[tm.id][j], z);
         }
       }
       if (i < NB) x[zoff + i] = z;
@@ -256,14 +262,18 @@ cudaError_t launch_bwd_kernel(const F64View &v, double *x, cudaStream_t st) {
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
-  return cudaLaunchKernelEx(&cfg, k_solve_bwd_tail<NB>, v, x, CS);
+  if (solve_capped(v.S, CS)) return cudaLaunchKernelEx(&cfg, k_solve_bwd_tail<NB, SolveCfg<NB>::MINB>, v, x, CS);
+  return cudaLaunchKernelEx(&cfg, k_solve_bwd_tail<NB, 1>, v, x, CS);
 }
 
 }  // namespace
 
 void f64_launch_solve_root(const F64View &v, const double *r, double *x, double *r0t, cudaStream_t st);
 
-#define BM_SOLVE_NB_LIST(X) X(2) X(3) X(4) X(6) X(8) X(12) X(16) X(24) X(32) X(48)
+// The cluster solves substitute with the scaled unit factor that the
+// compile-time tail factor stores above each diagonal block's diagonal, so
+// they cover exactly the tail factor's block sizes.
+#define BM_SOLVE_NB_LIST(X) BM_TAIL_NB_LIST(X)
 
 bool f64_cluster_solve_supported(int nb) {
   switch (nb) {
@@ -279,7 +289,8 @@ void f64_cluster_launch_solve(const F64View &v, const double *r, double *x, doub
   switch (v.nb) {
 #define X(n)                                                    \
   case n:                                                       \
-    launch_tail_kernel<n>(k_solve_fwd_tail<n>, v, r, st);       \
+    launch_tail_kernel<n>(solve_capped(v.S, pick_cluster(v.S)) ? k_solve_fwd_tail<n, SolveCfg<n>::MINB> \
+                                                               : k_solve_fwd_tail<n, 1>, v, r, st); \
     f64_launch_solve_root(v, r, x, r0t, st);                    \
     launch_bwd_kernel<n>(v, x, st);                             \
     break;

@@ -103,7 +103,7 @@ __device__ __forceinline__ void factor_task(const TailView<T> &v, const Team<TEA
   tm.sync();
   const int fail = team_chol<TEAM, NB, T>(tm, sD, sInv);
   if (tm.lane == 0 && fail) report_not_spd(v.status, s, N + 1 - q);
-  team_store_lower<TEAM, NB, T>(tm, v.Ld + (sb + (N - q)) * NB2, sD);
+  team_store_factor<TEAM, NB, T>(tm, v.Ld + (sb + (N - q)) * NB2, sD, sInv);
   team_trsm_lt<TEAM, NB, T>(tm, sB, hasA ? 2 * NB : NB, sD, sInv);
   team_copy<TEAM, NB2>(tm, v.Lr + (sb + (N - q)) * NB2, sB);
   if (hasA) {
@@ -147,7 +147,7 @@ __device__ __forceinline__ void x1_task(const TailView<T> &v, const Team<TEAM> &
   }
   const int fail = team_chol<TEAM, NB, T>(tm, sD, sInv);
   if (tm.lane == 0 && fail) report_not_spd(v.status, s, 1);
-  team_store_lower<TEAM, NB, T>(tm, v.Ld + sb * NB2, sD);
+  team_store_factor<TEAM, NB, T>(tm, v.Ld + sb * NB2, sD, sInv);
   team_zero<TEAM, NB2>(tm, v.Ll + sb * NB2);
   team_zero<TEAM, NB2>(tm, v.Lr + sb * NB2);
   team_copy<TEAM, NB>(tm, v.invd + sb * NB, sInv);

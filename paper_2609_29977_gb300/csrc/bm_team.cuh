@@ -186,6 +186,29 @@ __device__ __forceinline__ void team_store_lower(const Team<TEAM> &tm, T *__rest
   }
 }
 
+// Stores a diagonal factor block L (lower triangle of s, inverse diagonal
+// in inv). For T = double the strict upper triangle of g receives the
+// transpose of M = L diag(L)^-1, the unit lower triangular factor with
+// columns scaled by the inverse pivots: g[i][j] = L_ji * inv_i for i < j.
+// The tail solves then substitute with M and scale once (L y = z is
+// M w = z, y = inv .* w; L^T x = z is M^T x = inv .* z), one FP64
+// instruction per elimination step instead of two. For T = float the
+// upper triangle is zero.
+template <int TEAM, int NB, typename T>
+__device__ __forceinline__ void team_store_factor(const Team<TEAM> &tm, T *__restrict__ g, const T *__restrict__ s,
+                                                  const T *__restrict__ inv) {
+#pragma unroll
+  for (int e = tm.lane; e < NB * NB; e += TEAM) {
+    const int i = e / NB, j = e - i * NB;
+    T val = T(0);
+    if (j <= i)
+      val = s[e];
+    else if (sizeof(T) == sizeof(double))
+      val = s[j * NB + i] * inv[i];
+    g[e] = val;
+  }
+}
+
 // lower(sD) -= X X^T (+ Y Y^T when Y != null).
 template <int TEAM, int NB, typename T>
 __device__ __forceinline__ void team_syrk_sub(const Team<TEAM> &tm, T *sD, const T *X, const T *Y) {
