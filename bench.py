@@ -848,6 +848,7 @@ def run_gpu(args):
         "us_per_kkt": ms_per_step * 1e3, **meas,
         "forward_error_vs_fp64": fwd_vs_fp64, "refinement_steps": info.get("iters"),
         "device_status": info["name"],
+        "residual_float_float": info.get("residual_float_float") if args.precision == "fp32ir" else None,
         "flops_per_kkt": {"method": fl["total"], "natural_order_factor": bmgen.natural_flops(w.S, w.N, w.nb, w.nr)},
         "roofline": {"kernel": "factor pipeline (%s, one graph)" % _factor_kernels(w.N, w.nb, args.precision),
                      "bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "GFLOP/s",
@@ -901,6 +902,7 @@ def run_gpu(args):
             "value": world * fl["total"] / (mms * 1e-3) / 1e9, "unit": "GFLOP/s",
             "steps": k, **mmeas, "refinement_steps": minfo["iters"],
             "coupling_refined": minfo["coupling_refined"],
+            "residual_float_float": minfo["residual_float_float"],
             "forward_error_vs_fp64": float((xm - x).abs().max() / x.abs().max()),
             "device_status": minfo["name"], "speedup_vs_fp64": ms_per_step / mms,
             "gpu_launches_per_step": mixed.launches_per_step(minfo.get("iters"))}
@@ -931,7 +933,8 @@ def _schedule_of(solver, bm):
 
 def _coupling_flags(args):
     import paper_2609_29977_gb300 as bm
-    return {"auto": 0, "refine": bm.BM_FLAG_COUPLING_REFINE, "fp32": bm.BM_FLAG_COUPLING_FP32}[args.coupling]
+    f = {"auto": 0, "refine": bm.BM_FLAG_COUPLING_REFINE, "fp32": bm.BM_FLAG_COUPLING_FP32}[args.coupling]
+    return f | (bm.BM_FLAG_RESIDUAL_FP64 if args.residual == "fp64" else 0)
 
 
 def _sub_line(fn):
@@ -989,6 +992,8 @@ def main():
     ap.add_argument("--gen-device", default="cuda", help="batched: where the systems are drawn (cuda or cpu)")
     ap.add_argument("--coupling", default="auto", choices=["auto", "refine", "fp32"],
                     help="mixed precision: refine the coupling columns automatically, always, or never")
+    ap.add_argument("--residual", default="auto", choices=["auto", "fp64"],
+                    help="fp32ir refinement residual: float-float when tol >= 1e-11 (auto) or always FP64")
     ap.add_argument("--no-forms", action="store_true",
                     help="default workload: skip the batched and serving sub-runs reported beside the main line")
     args = ap.parse_args()

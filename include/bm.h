@@ -85,6 +85,9 @@ typedef enum {
 /* BM_PREC_FP64: keep the default launch schedule of the tail factor instead
  * of autotuning it on the first bm_factor (see bm_schedule) */
 #define BM_FLAG_NO_TUNE 8u
+/* BM_PREC_FP32_IR: compute every refinement residual with FP64 arithmetic,
+ * never in float-float (see bm_solve) */
+#define BM_FLAG_RESIDUAL_FP64 16u
 
 typedef struct {
   int S, N, nb, nr;   /* scenarios (the paper's M), horizon, stage block, root block */
@@ -101,6 +104,8 @@ typedef struct {
   int iters;           /* BM_PREC_FP32_IR: refinement steps of the last solve */
   double backward_error; /* BM_PREC_FP32_IR: componentwise backward error of the returned x; FP64: -1 */
   int coupling_refined;  /* BM_PREC_FP32_IR: 1 if the last bm_factor refined the coupling columns */
+  int residual_float_float; /* BM_PREC_FP32_IR: 1 if the refinement residuals of the last bm_solve were
+                               float-float, 0 if FP64 (see bm_solve) */
 } bm_info;
 
 /* Library version (BM_VERSION). */
@@ -146,10 +151,19 @@ bm_status bm_factor(bm_handle h, const double *D, const double *E, const double 
  * substitution with L_R, root propagation dy^i_1 -= F_{i,1}^T dx_0, tail
  * backward substitution and the inverse permutation. r and x are device
  * vectors of length S*N*nb + nr in natural order; x must not alias r.
- * BM_PREC_FP32_IR: iterative refinement on K with an FP64 residual until
- * the componentwise backward error
+ * BM_PREC_FP32_IR: iterative refinement on K with an FP64-accurate
+ * residual until the componentwise backward error
  *     omega = max_i |r - K x|_i / (|K| |x| + |r|)_i     (Oettli-Prager)
- * is <= tol. It reports BM_ERR_NOT_CONVERGED (x = the last iterate) after
+ * is <= tol. The residual r - K x is computed with FP64 arithmetic, or,
+ * when tol >= 1e-11 and BM_FLAG_RESIDUAL_FP64 is not set, in float-float
+ * on the FP32 pipe: K and x split into hi + lo floats (K once per
+ * bm_factor), exact products (Dekker's TwoProduct), Knuth's TwoSum for the
+ * running sum, FP64 accumulation of every 8 terms. Its error is at most
+ * beta = 4e-12 times (|K| |x|)_i, and the stopping test is then
+ * omega <= tol - beta, so the returned x still has omega <= tol. A system
+ * with a nonzero entry of K or x outside 2^-50..2^50 in magnitude falls
+ * back to FP64 residuals (bm_info.residual_float_float says which ran).
+ * It reports BM_ERR_NOT_CONVERGED (x = the last iterate) after
  * max_refine corrections, or earlier once omega fails to halve from one
  * correction to the next (stalled or diverging refinement). In the captured
  * graph the refinement iterations are a conditional loop that ends on the
@@ -159,6 +173,17 @@ bm_status bm_factor(bm_handle h, const double *D, const double *E, const double 
  * Errors: BM_ERR_INVALID_ARG, BM_ERR_NOT_FACTORED, BM_ERR_CUDA.
  */
 bm_status bm_solve(bm_handle h, const double *r, double *x, void *stream);
+
+/*
+ * BM_PREC_FP32_IR: rho = r - K x for the K of the last bm_factor, with the
+ * arithmetic of the handle's refinement residual (float-float or FP64, see
+ * bm_solve). r, x, rho: device vectors of length S*N*nb + nr in natural
+ * order; rho must alias neither. Overwrites the handle's split copy of the
+ * refinement iterate (the next bm_solve makes its own). Asynchronous.
+ * Errors: BM_ERR_INVALID_ARG (also for BM_PREC_FP64 handles),
+ * BM_ERR_NOT_FACTORED, BM_ERR_CUDA.
+ */
+bm_status bm_residual(bm_handle h, const double *r, const double *x, double *rho, void *stream);
 
 /*
  * Launch schedule of the FP64 factor (not in the paper; the factor's

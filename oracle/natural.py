@@ -152,6 +152,46 @@ def residual_rows(D, E, C, R, x, r, rows) -> dict:
     return {"rho": rho, "omega": float(om.max()) if om.size else 0.0}
 
 
+def residual_rows_exact(D, E, C, R, x, r, rows) -> dict:
+    """rho_i = r_i - (K x)_i computed exactly in rational arithmetic (every
+    FP64 entry is a dyadic rational, so each product and the sum are exact)
+    and rounded once to FP64, with (|K| |x|)_i, for a set of row indices of
+    K (natural order, the blocks of Eq. root_coupled_matrix as in
+    ``residual_rows``). The reference for residuals that claim more than
+    FP64 summation accuracy."""
+    from fractions import Fraction
+    D, E, C, R, x, r = (_f64(a) for a in (D, E, C, R, x, r))
+    S, N, nb, _ = D.shape
+    nr = R.shape[0]
+    n0 = S * N * nb
+    rows = np.asarray(rows, dtype=np.int64)
+    rho = np.zeros(rows.size)
+    kx = np.zeros(rows.size)
+    for t, g in enumerate(rows):
+        pairs = []
+        if g < n0:
+            s, rem = divmod(int(g), N * nb)
+            k, i = divmod(rem, nb)
+            base = s * N * nb
+            pairs += [(D[s, k, i, j] if j <= i else D[s, k, j, i], x[base + k * nb + j]) for j in range(nb)]
+            if k > 0:
+                pairs += [(E[s, k - 1, i, j], x[base + (k - 1) * nb + j]) for j in range(nb)]
+            if k + 1 < N:
+                pairs += [(E[s, k, j, i], x[base + (k + 1) * nb + j]) for j in range(nb)]
+            if k == 0:
+                pairs += [(C[s, j, i], x[n0 + j]) for j in range(nr)]
+        else:
+            c = int(g) - n0
+            pairs += [(R[c, j] if j <= c else R[j, c], x[n0 + j]) for j in range(nr)]
+            pairs += [(C[s, c, j], x[s * N * nb + j]) for s in range(S) for j in range(nb)]
+        acc = Fraction(float(r[g]))
+        for a, b in pairs:
+            acc -= Fraction(float(a)) * Fraction(float(b))
+        rho[t] = float(acc)
+        kx[t] = float(sum(abs(Fraction(float(a)) * Fraction(float(b))) for a, b in pairs))
+    return {"rho": rho, "abs_kx": kx}
+
+
 def residual(D, E, C, R, x, r, nthreads: int = 0) -> dict:
     """rho = r - K x in FP64, the normwise backward error
     eta = ||rho||_inf / (||K||_inf ||x||_inf + ||r||_inf), the componentwise

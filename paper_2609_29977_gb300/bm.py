@@ -19,6 +19,7 @@ BM_FLAG_NO_GRAPH = 1
 BM_FLAG_COUPLING_REFINE = 2   # mixed precision: always refine the coupling columns
 BM_FLAG_COUPLING_FP32 = 4     # mixed precision: never (root from the FP32 tail factor alone)
 BM_FLAG_NO_TUNE = 8           # FP64: keep the default launch schedule (no autotuning)
+BM_FLAG_RESIDUAL_FP64 = 16    # FP32_IR: FP64 refinement residuals, never float-float
 
 BM_OK = 0
 STATUS_NAMES = {0: "BM_OK", 1: "BM_ERR_INVALID_ARG", 2: "BM_ERR_NOT_SPD", 3: "BM_ERR_OOM",
@@ -26,7 +27,7 @@ STATUS_NAMES = {0: "BM_OK", 1: "BM_ERR_INVALID_ARG", 2: "BM_ERR_NOT_SPD", 3: "BM
                 7: "BM_ERR_NOT_FACTORED"}
 
 EXPORTED_SYMBOLS = ("bm_version", "bm_status_string", "bm_workspace_bytes", "bm_analyze", "bm_factor",
-                    "bm_solve", "bm_query", "bm_schedule", "bm_export_factor", "bm_factor_solve_host", "bm_destroy",
+                    "bm_solve", "bm_residual", "bm_query", "bm_schedule", "bm_export_factor", "bm_factor_solve_host", "bm_destroy",
                     "bm_factor_solve_noalloc", "bm_round_to_fp32", "bm_batch_workspace_bytes",
                     "bm_batch_analyze", "bm_batch_factor", "bm_batch_solve", "bm_batch_query",
                     "bm_batch_schedule", "bm_batch_destroy", "bm_server_request_bytes", "bm_server_create",
@@ -48,7 +49,8 @@ class bm_desc(ctypes.Structure):
 
 class bm_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("fail_scenario", ctypes.c_int), ("fail_stage", ctypes.c_int),
-                ("iters", ctypes.c_int), ("backward_error", ctypes.c_double), ("coupling_refined", ctypes.c_int)]
+                ("iters", ctypes.c_int), ("backward_error", ctypes.c_double), ("coupling_refined", ctypes.c_int),
+                ("residual_float_float", ctypes.c_int)]
 
 
 class bm_qp_desc(ctypes.Structure):
@@ -117,6 +119,8 @@ def _load():
     lib.bm_factor.argtypes = [vp, dp, dp, dp, dp, vp]
     lib.bm_solve.restype = ctypes.c_int
     lib.bm_solve.argtypes = [vp, dp, dp, vp]
+    lib.bm_residual.restype = ctypes.c_int
+    lib.bm_residual.argtypes = [vp, dp, dp, dp, vp]
     lib.bm_query.restype = ctypes.c_int
     lib.bm_query.argtypes = [vp, vp, ctypes.POINTER(bm_info)]
     lib.bm_export_factor.restype = ctypes.c_int
@@ -223,7 +227,17 @@ def top_level(N: int) -> int:
     return chain_levels(N)
 
 
-def launches_per_step(S, N, nb, nr, precision=BM_PREC_FP64, max_refine=10, iters=None, flags=0) -> int:
+FF_RESIDUAL_MIN_TOL = 1e-11   # FP32_IR: float-float refinement residuals from this tolerance up
+
+
+def ff_residual(tol=1e-10, flags=0) -> bool:
+    """Whether a BM_PREC_FP32_IR handle computes float-float residuals."""
+    tol = tol if tol > 0 else 1e-10
+    return not (flags & BM_FLAG_RESIDUAL_FP64) and tol >= FF_RESIDUAL_MIN_TOL
+
+
+def launches_per_step(S, N, nb, nr, precision=BM_PREC_FP64, max_refine=10, iters=None, flags=0,
+                      tol=1e-10) -> int:
     """Kernels that one bm_factor + one bm_solve launch.
 
     Factor: one launch per level below ``top_level(N)``, one for the top
@@ -243,16 +257,19 @@ def launches_per_step(S, N, nb, nr, precision=BM_PREC_FP64, max_refine=10, iters
     iteration; pass the corrections of the solve
     (``query()["iters"]``) for a captured graph, whose loop stops after the
     last iteration that runs; without it the count is the unrolled
-    direct-launch bound (``max_refine <= 0`` selects 10)."""
+    direct-launch bound (``max_refine <= 0`` selects 10). With float-float
+    refinement residuals (``ff_residual(tol, flags)``) the mixed factor
+    first splits K into hi + lo floats: one more launch."""
     Lc = chain_levels(N)
     if precision == BM_PREC_FP32_IR:
         mr = max_refine if max_refine > 0 else 10
         runs = mr + 1 if iters is None else min(int(iters), mr) + 1
+        split = 1 if ff_residual(tol, flags) else 0
         if flags & BM_FLAG_COUPLING_FP32:
-            return (top_level(N) + 2) + 3 * runs
+            return split + (top_level(N) + 2) + 3 * runs
         # refined coupling columns: the first correction's root terms are
         # one more launch per solve (it returns at once when not refined)
-        factor = top_level(N) + (6 if flags & BM_FLAG_COUPLING_REFINE else 8)
+        factor = split + top_level(N) + (6 if flags & BM_FLAG_COUPLING_REFINE else 8)
         return factor + 1 + 3 * runs
     if nb not in TAIL_NB:
         return (Lc + 2) + (2 * Lc + 3)
@@ -282,12 +299,18 @@ def bm_solve(h, r, x, stream=None) -> None:
     _check(_load().bm_solve(h, _ptr(r, "r"), _ptr(x, "x"), _stream(stream)), "bm_solve")
 
 
+def bm_residual(h, r, x, rho, stream=None) -> None:
+    """rho = r - K x with the handle's refinement arithmetic (FP32_IR handles)."""
+    _check(_load().bm_residual(h, _ptr(r, "r"), _ptr(x, "x"), _ptr(rho, "rho"), _stream(stream)), "bm_residual")
+
+
 def bm_query(h, stream=None) -> dict:
     info = bm_info()
     code = _load().bm_query(h, _stream(stream), ctypes.byref(info))
     return {"status": int(code), "name": STATUS_NAMES.get(int(code), str(code)),
             "fail_scenario": info.fail_scenario, "fail_stage": info.fail_stage, "iters": info.iters,
-            "backward_error": info.backward_error, "coupling_refined": int(info.coupling_refined)}
+            "backward_error": info.backward_error, "coupling_refined": int(info.coupling_refined),
+            "residual_float_float": int(info.residual_float_float)}
 
 
 def bm_schedule(h) -> dict:
@@ -357,11 +380,19 @@ class BranchKKTSolver:
         bm_solve(self.h, r, x, stream)
         return x
 
+    def residual(self, r, x, rho=None, stream=None):
+        import torch
+        if rho is None:
+            rho = torch.empty_like(r)
+        bm_residual(self.h, r, x, rho, stream)
+        return rho
+
     def launches_per_step(self, iters=None) -> int:
         """Kernels one bm_factor + one bm_solve of this handle launch (see
         the module-level ``launches_per_step``)."""
         S, N, nb, nr = self.shape
-        return launches_per_step(S, N, nb, nr, self.desc.precision, self.desc.max_refine, iters, self.desc.flags)
+        return launches_per_step(S, N, nb, nr, self.desc.precision, self.desc.max_refine, iters, self.desc.flags,
+                                 self.desc.tol)
 
     def query(self, stream=None) -> dict:
         return bm_query(self.h, stream)

@@ -27,9 +27,12 @@ void f64_launch_export_ld(const F64View &v, double *Ld, cudaStream_t st);
 
 // mixed precision path (bm_mixed.cu)
 struct MixedState;
-size_t mixed_bytes(int S, int N, int nb, int nr, int cmode);
+size_t mixed_bytes(int S, int N, int nb, int nr, int cmode, int ff);
+bool mixed_ff_residual(double tol, unsigned flags);
+bool mixed_ffres(const MixedState *m);
+void mixed_launch_residual(MixedState *m, const double *r, const double *x, double *rho, cudaStream_t st);
 cudaError_t mixed_prepare(int nb, int nr);
-MixedState *mixed_create(int S, int N, int nb, int nr, int cmode, void *base, size_t bytes, Status *status,
+MixedState *mixed_create(int S, int N, int nb, int nr, int cmode, int ff, void *base, size_t bytes, Status *status,
                          unsigned *tickets, cudaStream_t init_stream, bool sync_init);
 void mixed_destroy(MixedState *m);
 void mixed_launch_factor(MixedState *m, const double *D, const double *E, const double *C,
@@ -94,6 +97,12 @@ static int coupling_mode(const bm_desc *d) {
   return 1;
 }
 
+// Float-float refinement residual of the mixed path (1) or FP64 (0): by the
+// tolerance (<= 0 means the default 1e-10) and BM_FLAG_RESIDUAL_FP64.
+static int ff_mode(const bm_desc *d) {
+  return mixed_ff_residual(d->tol > 0.0 ? d->tol : 1e-10, d->flags) ? 1 : 0;
+}
+
 static size_t f64_bytes(int S, int N, int nb, int nr) {
   const size_t SN = (size_t)S * N, b2 = (size_t)nb * nb;
   size_t t = 0;
@@ -131,7 +140,7 @@ extern "C" size_t bm_workspace_bytes(const bm_desc *d) {
   if (d->precision == BM_PREC_FP64)
     t += f64_bytes(d->S, d->N, d->nb, d->nr);
   else
-    t += mixed_bytes(d->S, d->N, d->nb, d->nr, coupling_mode(d));
+    t += mixed_bytes(d->S, d->N, d->nb, d->nr, coupling_mode(d), ff_mode(d));
   return t;
 }
 
@@ -192,7 +201,7 @@ bm_status analyze_impl(const bm_desc *desc, void *mem, size_t bytes, cudaStream_
     if (f64_prepare(nb, nr) != cudaSuccess) goto cuda_fail;
   } else {
     if (mixed_prepare(nb, nr) != cudaSuccess) goto cuda_fail;
-    h->mixed = mixed_create(S, N, nb, nr, coupling_mode(desc), (char *)h->pool + kHeader, h->pool_bytes - kHeader, h->status,
+    h->mixed = mixed_create(S, N, nb, nr, coupling_mode(desc), ff_mode(desc), (char *)h->pool + kHeader, h->pool_bytes - kHeader, h->status,
                             h->tickets, light ? init_stream : nullptr, !light);
     if (!h->mixed) goto cuda_fail;
   }
@@ -388,6 +397,15 @@ extern "C" bm_status bm_solve(bm_handle h, const double *r, double *x, void *str
   return run(h, h->gsol, key, 2, st, [&](cudaStream_t cs, bool) { f64_launch_solve(v, r, x, r0t, cs); });
 }
 
+extern "C" bm_status bm_residual(bm_handle h, const double *r, const double *x, double *rho, void *stream) {
+  if (!h || !r || !x || !rho || !h->mixed) return BM_ERR_INVALID_ARG;
+  if (!aligned16(r) || !aligned16(x) || !aligned16(rho)) return BM_ERR_INVALID_ARG;
+  if ((const void *)rho == (const void *)r || (const void *)rho == (const void *)x) return BM_ERR_INVALID_ARG;
+  if (!h->factored) return BM_ERR_NOT_FACTORED;
+  mixed_launch_residual(h->mixed, r, x, rho, (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? BM_OK : BM_ERR_CUDA;
+}
+
 extern "C" bm_status bm_schedule(bm_handle h, int *top_level, int *team_per_level, int *source) {
   if (!h) return BM_ERR_INVALID_ARG;
   if (h->mixed || !tail_nb_supported(h->desc.nb)) return BM_ERR_INVALID_ARG;
@@ -417,6 +435,7 @@ extern "C" bm_status bm_query(bm_handle h, void *stream, bm_info *info) {
     info->iters = h->mixed ? st.iters : 0;
     info->backward_error = h->mixed ? st.eta : -1.0;
     info->coupling_refined = h->mixed ? st.coupled : 0;
+    info->residual_float_float = h->mixed && mixed_ffres(h->mixed) && !st.ffbad ? 1 : 0;
   }
   return (bm_status)st.code;
 }

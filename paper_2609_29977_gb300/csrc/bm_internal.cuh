@@ -61,6 +61,7 @@ struct Status {
   int iters;      // refinement steps
   int coupled;    // mixed precision: the coupling columns were refined in the last factor
   unsigned spread; // mixed precision: max over tails of (max/min FP32 pivot)^2, float bits
+  int ffbad;      // mixed precision: an entry of K or x is outside the float-float residual's range
   double eta;     // refinement: componentwise backward error of the iterate
 };
 

@@ -90,12 +90,24 @@ __global__ void __launch_bounds__(256) k_mixed_residual(MixedState m, const doub
   if (ir_done(m.ctl)) return;
   const int it = ir_iter(m.ctl, iter);
   const long nrow = (long)m.S * m.N * NB;
+  // float-float unless the handle computes FP64 residuals or an entry of K
+  // or x left the float-float range (uniform over the grid)
+  const bool ffr = m.ffres && __ldcg(&m.status->ffbad) == 0;
   float om = 0.0f;
-  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < nrow; e += (long)gridDim.x * blockDim.x) {
-    const long br = e / NB;
-    const int i = (int)(e - br * NB);
-    const int s = (int)(br / m.N), k = (int)(br - (long)s * m.N);
-    om = fmaxf(om, residual_row<NB>(m, r, x, s, k, i));
+  if (ffr) {
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < nrow; e += (long)gridDim.x * blockDim.x) {
+      const long br = e / NB;
+      const int i = (int)(e - br * NB);
+      const int s = (int)(br / m.N), k = (int)(br - (long)s * m.N);
+      om = fmaxf(om, residual_row_ff<NB>(m, r, x, s, k, i));
+    }
+  } else {
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < nrow; e += (long)gridDim.x * blockDim.x) {
+      const long br = e / NB;
+      const int i = (int)(e - br * NB);
+      const int s = (int)(br / m.N), k = (int)(br - (long)s * m.N);
+      om = fmaxf(om, residual_row<NB>(m, r, x, s, k, i));
+    }
   }
   omega_publish(m.ctl, om);
   // each thread reads back only the rho rows it wrote
@@ -110,7 +122,7 @@ __global__ void __launch_bounds__(256) k_mixed_residual(MixedState m, const doub
   __syncthreads();
   if (threadIdx.x == 0 && sroot) atomicMax(&m.ctl->wmax, sroot);
   if (last_cta(&m.tickets[3], gridDim.x) && threadIdx.x == 0) {
-    const bool more = ir_stop(m, 0.0f, it, max_iter, tol);
+    const bool more = ir_stop(m, 0.0f, it, max_iter, ffr ? tol - kFFBeta : tol);
     if (iter < 0 && more) cudaGraphSetConditional(cond, 1u);
   }
 }
@@ -166,6 +178,69 @@ __global__ void __launch_bounds__(256) k_pivot_spread(const float *__restrict__ 
 __global__ void k_widen(const float *__restrict__ src, double *__restrict__ dst, size_t n) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     dst[i] = f2d_exact(src[i]);
+}
+
+// K split into hi + lo floats for the float-float residual: D as full
+// symmetric rows (its lower triangle mirrored), E as stored. Sets
+// status->ffbad if a nonzero entry is outside the float-float range.
+template <int NB>
+__global__ void __launch_bounds__(256) k_ff_split(MixedState m) {
+  constexpr int NB2 = NB * NB;
+  pdl_wait();
+  const long nd = (long)m.S * m.N * NB2, ne = (long)m.S * (m.N - 1) * NB2;
+  bool bad = false;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < nd + ne; e += (long)gridDim.x * blockDim.x) {
+    double v;
+    float h, l;
+    if (e < nd) {
+      const long blk = e / NB2;
+      const int w = (int)(e - blk * NB2), i = w / NB, j = w - i * NB;
+      v = j <= i ? m.D[e] : m.D[blk * NB2 + j * NB + i];
+      ff::split_d(v, h, l);
+      m.Kdh[e] = h;
+      m.Kdl[e] = l;
+    } else {
+      v = m.E[e - nd];
+      ff::split_d(v, h, l);
+      m.Keh[e - nd] = h;
+      m.Kel[e - nd] = l;
+    }
+    bad |= ff_out_of_range(v);
+  }
+  if (bad) m.status->ffbad = 1;
+  pdl_trigger();
+}
+
+// x split into hi + lo floats (bm_residual; the refinement splits its
+// iterate in the backward kernel).
+__global__ void __launch_bounds__(256) k_x_split(MixedState m, const double *__restrict__ x) {
+  const long n = (long)m.S * m.N * m.nb;
+  bool bad = false;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+    const double v = x[e];
+    ff::split_d(v, m.xh[e], m.xl[e]);
+    bad |= ff_out_of_range(v);
+  }
+  if (bad) m.status->ffbad = 1;
+}
+
+// rho = r - K x with the refinement's arithmetic (bm_residual): m.rho is
+// the caller's array.
+template <int NB>
+__global__ void __launch_bounds__(256) k_residual_out(MixedState m, const double *__restrict__ r,
+                                                       const double *__restrict__ x) {
+  const long nrow = (long)m.S * m.N * NB;
+  const bool ffr = m.ffres && __ldcg(&m.status->ffbad) == 0;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < nrow; e += (long)gridDim.x * blockDim.x) {
+    const long br = e / NB;
+    const int i = (int)(e - br * NB);
+    const int s = (int)(br / m.N), k = (int)(br - (long)s * m.N);
+    if (ffr)
+      residual_row_ff<NB>(m, r, x, s, k, i);
+    else
+      residual_row<NB>(m, r, x, s, k, i);
+  }
+  for (int c = blockIdx.x; c < m.nr; c += gridDim.x) residual_root_row(m, r, x, NB, c);
 }
 
 int pick_cluster(int S) {
@@ -268,8 +343,8 @@ cudaError_t capture_loop(const MixedState &m, const double *r, double *x, int ma
 static int coupling_ldc(int nr) { return (nr + cx::RC - 1) / cx::RC * cx::RC; }
 
 // cmode: 0 = the FP32-based root (no coupling buffers), 1 = automatic,
-// 2 = always refine the coupling columns.
-size_t mixed_bytes(int S, int N, int nb, int nr, int cmode) {
+// 2 = always refine the coupling columns. ff: float-float residual buffers.
+size_t mixed_bytes(int S, int N, int nb, int nr, int cmode, int ff) {
   const size_t SN = (size_t)S * N, b2 = (size_t)nb * nb, n = SN * nb + nr;
   size_t t = 0;
   t += align_up(SN * b2 * sizeof(float), 256) * 5;          // Ld Ll Lr Dt W
@@ -287,10 +362,22 @@ size_t mixed_bytes(int S, int N, int nb, int nr, int cmode) {
     t += xb;                          // Xa
     if (ldc > nb) t += 2 * xb;        // Yb, Zr (else they reuse W and Dt)
   }
+  if (ff) {
+    t += align_up(SN * b2 * sizeof(float), 256) * 2;                        // Kdh Kdl
+    t += align_up((size_t)S * (N > 1 ? N - 1 : 0) * b2 * sizeof(float), 256) * 2;  // Keh Kel
+    t += align_up(SN * nb * sizeof(float), 256) * 2;                        // xh xl
+  }
   return t;
 }
 
-size_t mixed_bytes(int S, int N, int nb, int nr) { return mixed_bytes(S, N, nb, nr, 0); }
+size_t mixed_bytes(int S, int N, int nb, int nr) { return mixed_bytes(S, N, nb, nr, 0, 0); }
+
+// Whether a handle with tolerance tol computes float-float residuals.
+bool mixed_ff_residual(double tol, unsigned flags) {
+  return !(flags & BM_FLAG_RESIDUAL_FP64) && tol >= mx::kFFMinTol;
+}
+
+bool mixed_ffres(const MixedState *m) { return m->ffres != 0; }
 
 
 cudaError_t mixed_prepare(int nb, int nr) {
@@ -307,9 +394,9 @@ cudaError_t mixed_prepare(int nb, int nr) {
   return e;
 }
 
-MixedState *mixed_create(int S, int N, int nb, int nr, int cmode, void *base, size_t bytes, Status *status,
-                         unsigned *tickets, cudaStream_t init_stream, bool sync_init) {
-  if (bytes < mixed_bytes(S, N, nb, nr, cmode)) return nullptr;
+MixedState *mixed_create(int S, int N, int nb, int nr, int cmode, int ff, void *base, size_t bytes,
+                         Status *status, unsigned *tickets, cudaStream_t init_stream, bool sync_init) {
+  if (bytes < mixed_bytes(S, N, nb, nr, cmode, ff)) return nullptr;
   MixedState *m = new (std::nothrow) MixedState();
   if (!m) return nullptr;
   m->S = S; m->N = N; m->nb = nb; m->nr = nr; m->Lc = chain_levels(N);
@@ -343,6 +430,13 @@ MixedState *mixed_create(int S, int N, int nb, int nr, int cmode, void *base, si
       m->Zr = m->Dt;
     }
   }
+  if (ff) {
+    const size_t ne = (size_t)S * (N > 1 ? N - 1 : 0) * b2;
+    m->ffres = 1;
+    m->Kdh = (float *)take(SN * b2 * 4); m->Kdl = (float *)take(SN * b2 * 4);
+    m->Keh = (float *)take(ne * 4); m->Kel = (float *)take(ne * 4);
+    m->xh = (float *)take(SN * nb * 4); m->xl = (float *)take(SN * nb * 4);
+  }
   m->status = status;
   m->tickets = tickets;
   if ((sync_init ? cudaMemset(m->ctl, 0, sizeof(IRCtl)) : cudaMemsetAsync(m->ctl, 0, sizeof(IRCtl), init_stream)) !=
@@ -368,6 +462,19 @@ void mixed_launch_factor(MixedState *m, const double *D, const double *E, const 
   t.D = D; t.E = E; t.C = C; t.R = R;
   t.Ld = m->Ld; t.Ll = m->Ll; t.Lr = m->Lr; t.Dt = m->Dt; t.W = m->W; t.invd = m->invd;
   t.F = m->F; t.U = m->U; t.status = m->status;
+  if (m->ffres) {
+    const long n = (long)m->S * (2 * m->N - 1) * m->nb * m->nb;
+    long blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    switch (m->nb) {
+#define X(n)                                                                       \
+  case n:                                                                          \
+    launch_plain(k_ff_split<n>, (unsigned)blocks, 256, 0, true, st, *m);           \
+    break;
+      BM_TAIL_NB_LIST(X)
+#undef X
+    }
+  }
   tail_factor_launch<float>(t, st);
   int *on = &m->status->coupled;
   if (m->cmode == 0) {
@@ -429,6 +536,28 @@ cudaError_t mixed_launch_solve(MixedState *m, const double *r, double *x, int ma
   return cudaPeekAtLastError();
 }
 
+
+// rho = r - K x for the last factor's K, float-float or FP64 as the
+// refinement of this handle computes it.
+void mixed_launch_residual(MixedState *m, const double *r, const double *x, double *rho, cudaStream_t st) {
+  MixedState c = *m;
+  c.rho = rho;
+  const long n = (long)m->S * m->N * m->nb;
+  if (m->ffres) {
+    long blocks = (n + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_x_split<<<(unsigned)blocks, 256, 0, st>>>(c, x);
+  }
+  const int blocks = xt_blocks(m->S, m->N, m->nb, m->nr);
+  switch (m->nb) {
+#define X(n)                                                        \
+  case n:                                                           \
+    k_residual_out<n><<<(unsigned)blocks, 256, 0, st>>>(c, r, x); \
+    break;
+    BM_TAIL_NB_LIST(X)
+#undef X
+  }
+}
 
 void mixed_launch_export(MixedState *m, double *Ld, double *Ll, double *Lr, double *F, double *LR,
                          cudaStream_t st) {

@@ -32,6 +32,12 @@ struct MixedState {
   int cmode;                             // 0: FP32-based root, 1: automatic, 2: always refine
   float *Xa, *Yb, *Zr;                   // coupling refinement buffers (Xa = Xc)
   double *rho;                           // [n] residual
+  // float-float refinement residual (ffres = 1; else FP64): K split into
+  // hi + lo floats once per factor (Kd: D as full symmetric rows
+  // [S][N][nb][nb]; Ke: E as stored), the iterate x split by the backward
+  // kernel ([S][N][nb])
+  int ffres;
+  float *Kdh, *Kdl, *Keh, *Kel, *xh, *xl;
   IRCtl *ctl;
   Status *status;
   unsigned *tickets;
@@ -60,6 +66,14 @@ __device__ __forceinline__ float abs_f32_approx(double x) {
   if (e <= 0) return 0.0f;
   if (e >= 255) return __uint_as_float(0x7f7fffffu);
   return __uint_as_float(((unsigned)e << 23) | ((hi & 0xfffffu) << 3));
+}
+
+// The float-float residual's range: nonzero magnitudes in [2^-50, 2^50),
+// so that every product of hi and lo parts it forms is a normal float.
+__device__ __forceinline__ bool ff_out_of_range(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d) & 0x7fffffffu, lo = (unsigned)__double2loint(d);
+  const unsigned e = hi >> 20;
+  return (hi | lo) != 0u && (e < 1023u - 50u || e >= 1023u + 50u);
 }
 
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
@@ -470,7 +484,15 @@ __device__ __forceinline__ void bwd_tail(const MixedState &m, double *x, int ite
         } else {
           dz = f2d_exact(z);
         }
-        x[zoff + i] = iter == 0 ? dz : x[zoff + i] + dz;
+        const double xv = iter == 0 ? dz : x[zoff + i] + dz;
+        x[zoff + i] = xv;
+        if (m.ffres) {
+          float h, l;
+          ff::split_d(xv, h, l);
+          m.xh[zoff + i] = h;
+          m.xl[zoff + i] = l;
+          if (ff_out_of_range(xv)) m.status->ffbad = 1;
+        }
       }
       tm.sync();
     }
@@ -544,6 +566,115 @@ __device__ __forceinline__ float residual_row(const MixedState &m, const double 
   }
   m.rho[off + i] = acc;
   return omega_of(acc, w);
+}
+
+// Float-float residual (refinement with ffres = 1). The FP64 entries of K
+// and x are split into hi + lo floats (|v - hi - lo| <= 2^-48 |v|). Per
+// term, hi*hi is formed exactly (TwoProduct, bm_ff.cuh) and its high part
+// summed with TwoSum; the rounding errors of both and the cross terms
+// hi*lo + lo*hi go to a low FP32 sum (lo*lo, below 2^-48 |K||x|, is
+// dropped). Every 8 terms both sums are added to an FP64 accumulator, so
+// the low sum never holds more than 8 terms' worth:
+//   |rho_ff - rho|_i <= (8 * 4 * 11 + 3) 2^-48 (|K||x|)_i + O(2^-53)
+//                    ~ 1.3e-12 (|K||x|)_i,
+// below kFFBeta. With the stopping test omega <= tol - kFFBeta the exact
+// omega of an accepted iterate is <= tol.
+constexpr double kFFBeta = 4e-12;
+// Smallest tolerance refined with float-float residuals (2.5 kFFBeta): the
+// stopping test then still accepts omega up to 0.6 tol.
+constexpr double kFFMinTol = 1e-11;
+
+template <int NB, int STRIDE>
+__device__ __forceinline__ void ff_block(double &acc, float &w, const float *__restrict__ kh,
+                                         const float *__restrict__ kl, const float *__restrict__ xh,
+                                         const float *__restrict__ xl) {
+  constexpr bool V4 = STRIDE == 1 && NB % 4 == 0;
+#pragma unroll
+  for (int j0 = 0; j0 < NB; j0 += 8) {
+    constexpr int CH = 8;
+    float a[CH], al[CH], b[CH], bl[CH];
+    const int cnt = NB - j0 < CH ? NB - j0 : CH;
+    if constexpr (V4) {
+#pragma unroll
+      for (int g = 0; g < CH / 4; ++g) {
+        if (4 * g < cnt) {
+          const float4 va = *reinterpret_cast<const float4 *>(kh + j0 + 4 * g);
+          const float4 vl = *reinterpret_cast<const float4 *>(kl + j0 + 4 * g);
+          const float4 vb = __ldg(reinterpret_cast<const float4 *>(xh + j0 + 4 * g));
+          const float4 vc = __ldg(reinterpret_cast<const float4 *>(xl + j0 + 4 * g));
+          a[4 * g] = va.x; a[4 * g + 1] = va.y; a[4 * g + 2] = va.z; a[4 * g + 3] = va.w;
+          al[4 * g] = vl.x; al[4 * g + 1] = vl.y; al[4 * g + 2] = vl.z; al[4 * g + 3] = vl.w;
+          b[4 * g] = vb.x; b[4 * g + 1] = vb.y; b[4 * g + 2] = vb.z; b[4 * g + 3] = vb.w;
+          bl[4 * g] = vc.x; bl[4 * g + 1] = vc.y; bl[4 * g + 2] = vc.z; bl[4 * g + 3] = vc.w;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < CH; ++t) {
+        if (t < cnt) {
+          a[t] = kh[(j0 + t) * STRIDE];
+          al[t] = kl[(j0 + t) * STRIDE];
+          b[t] = __ldg(xh + j0 + t);
+          bl[t] = __ldg(xl + j0 + t);
+        }
+      }
+    }
+    float sh = 0.0f, c = 0.0f;
+#pragma unroll
+    for (int t = 0; t < CH; ++t) {
+      if (t < cnt) {
+        float p, ep, es;
+        ff::two_prod(a[t], b[t], p, ep);
+        ff::two_sum(sh, p, sh, es);
+        c = __fadd_rn(c, __fadd_rn(es, ep));
+        c = __fmaf_rn(a[t], bl[t], c);
+        c = __fmaf_rn(al[t], b[t], c);
+        w = __fmaf_rd(fabsf(a[t]), fabsf(b[t]), w);
+      }
+    }
+    acc += f2d_exact(sh);
+    acc += f2d_exact(c);
+  }
+}
+
+// Row i of block row (s, k) of the residual in float-float; as
+// residual_row, but (|K||x|)_i from the hi parts (scaled down by 2^-22 to
+// cover their rounding, so omega is never understated).
+template <int NB>
+__device__ __forceinline__ float residual_row_ff(const MixedState &m, const double *__restrict__ r,
+                                                 const double *__restrict__ x, int s, int k, int i) {
+  constexpr int NB2 = NB * NB;
+  const int N = m.N, nr = m.nr;
+  const size_t n0 = (size_t)m.S * N * NB;
+  const long br = (long)s * N + k;
+  const size_t off = (size_t)br * NB;
+  double acc = 0.0;
+  float w = 0.0f;
+  {
+    const size_t kb = (size_t)br * NB2 + (size_t)i * NB;
+    ff_block<NB, 1>(acc, w, m.Kdh + kb, m.Kdl + kb, m.xh + off, m.xl + off);
+  }
+  if (k > 0) {   // block (k, k-1) = E_k: row i
+    const size_t eb = ((size_t)s * (N - 1) + (k - 1)) * NB2 + (size_t)i * NB;
+    ff_block<NB, 1>(acc, w, m.Keh + eb, m.Kel + eb, m.xh + off - NB, m.xl + off - NB);
+  }
+  if (k + 1 < N) {   // block (k, k+1) = E_{k+1}^T: column i of E_{k+1}
+    const size_t eb = ((size_t)s * (N - 1) + k) * NB2 + i;
+    ff_block<NB, NB>(acc, w, m.Keh + eb, m.Kel + eb, m.xh + off + NB, m.xl + off + NB);
+  }
+  const double ri = r[off + i];
+  double rho = ri - acc;
+  w = __fadd_rd(__fmul_rd(w, __int_as_float(0x3f7ffffc)), abs_f32_approx(ri));   // 1 - 2^-22
+  if (k == 0) {   // block (1, root) = C_s^T, in FP64
+    const double *Cs = m.C + (size_t)s * nr * NB + i;
+    const double *x0 = x + n0;
+    for (int j = 0; j < nr; ++j) {
+      rho = fma(-Cs[j * NB], x0[j], rho);
+      w = fmaf(abs_f32_approx(Cs[j * NB]), abs_f32_approx(x0[j]), w);
+    }
+  }
+  m.rho[off + i] = rho;
+  return omega_of(rho, w);
 }
 
 // Folds a lane's omega into the warp and then into the system's wmax.

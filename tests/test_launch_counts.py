@@ -32,7 +32,8 @@ def test_fp64_counts():
 
 
 def test_mixed_counts():
-    fp32 = core.BM_FLAG_COUPLING_FP32
+    # FP64 refinement residuals (the float-float split kernel is counted below)
+    fp32 = core.BM_FLAG_COUPLING_FP32 | core.BM_FLAG_RESIDUAL_FP64
     # medium, FP32-based root, 2 corrections in a captured graph: 6 factor + 3 x 3 solve
     assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2, flags=fp32) == 15
     # directly launched: all 11 iterations
@@ -44,9 +45,15 @@ def test_mixed_counts():
     # bwd X0, residual, fwd, bwd correction, root; the solve adds the first
     # correction's root terms
     assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2,
-                                  flags=core.BM_FLAG_COUPLING_REFINE) == 10 + 1 + 9
+                                  flags=core.BM_FLAG_COUPLING_REFINE | core.BM_FLAG_RESIDUAL_FP64) == 10 + 1 + 9
     # automatic (default): pivot-spread reduction and probing root in addition
-    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2) == 12 + 1 + 9
+    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2,
+                                  flags=core.BM_FLAG_RESIDUAL_FP64) == 12 + 1 + 9
+    # float-float residuals (tol >= 1e-11, the default 1e-10): one split launch in the factor
+    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2) == 1 + 12 + 1 + 9
+    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2, tol=1e-11) == 1 + 12 + 1 + 9
+    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2, tol=1e-12) == 12 + 1 + 9
+    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2, tol=0) == 1 + 12 + 1 + 9
     # the mixed workload (N = 128: levels 0..6, top level 5): 6 tail launches
     assert core.top_level(128) == 5
-    assert core.launches_per_step(512, 128, 24, 8, core.BM_PREC_FP32_IR, 8, iters=3) == 13 + 1 + 12
+    assert core.launches_per_step(512, 128, 24, 8, core.BM_PREC_FP32_IR, 8, iters=3) == 1 + 13 + 1 + 12

@@ -395,3 +395,33 @@ def test_residual_rows_matches_dense_rows(S, N, nb, nr):
     assert np.allclose(got["rho"], d["r"] - K @ x, rtol=1e-12, atol=1e-12 * np.abs(K @ x).max())
     want = (np.abs(d["r"] - K @ x) / (np.abs(K) @ np.abs(x) + np.abs(d["r"]))).max()
     assert got["omega"] == pytest.approx(want, rel=1e-9)
+
+
+def test_exact_residual_rows():
+    """residual_rows_exact: zero residual where r = K x holds exactly (small
+    integer entries, where the FP64 product K x is itself exact), agreement
+    with the FP64 rows to FP64 rounding elsewhere, and the exact value where
+    FP64 summation cancels to zero."""
+    d = small(2, 5, 3, 2, seed=4, barrier=(-1, 1))
+    g = np.random.default_rng(7)
+    D, E, C, R = (np.round(4 * np.asarray(d[k])) for k in ("D", "E", "C", "R"))
+    x = g.integers(-5, 6, size=2 * 5 * 3 + 2).astype(np.float64)
+    K = dense.assemble_system(D, E, C, R)
+    r = K @ x                                   # exact: small integers
+    rows = np.arange(K.shape[0])
+    ex = natural.residual_rows_exact(D, E, C, R, x, r, rows)
+    assert np.array_equal(ex["rho"], np.zeros(rows.size))
+    assert np.allclose(ex["abs_kx"], np.abs(K) @ np.abs(x))
+    y = g.standard_normal(x.size)
+    ex = natural.residual_rows_exact(d["D"], d["E"], d["C"], d["R"], y, d["r"], rows)
+    Kd = dense.assemble_system(d["D"], d["E"], d["C"], d["R"])
+    assert np.allclose(ex["rho"], np.asarray(d["r"]) - Kd @ y, rtol=0,
+                       atol=1e-13 * (np.abs(Kd) @ np.abs(y)).max())
+    # a row whose FP64 sum, left to right, loses the 1: 1e16 * 1 + 1 * 1 + 1e16 * (-1)
+    D1 = np.zeros((1, 1, 3, 3))
+    D1[0, 0, 2] = [1e16, 1.0, 1e16]
+    C1, R1, E1 = np.zeros((1, 1, 3)), np.eye(1), np.zeros((1, 0, 3, 3))
+    x1, r1 = np.array([1.0, 1.0, -1.0, 0.0]), np.zeros(4)
+    assert (1e16 * 1.0 + 1.0 * 1.0) + 1e16 * -1.0 == 0.0
+    ex = natural.residual_rows_exact(D1, E1, C1, R1, x1, r1, [2])
+    assert ex["rho"][0] == -1.0 and ex["abs_kx"][0] == 2e16 + 1
