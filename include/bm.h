@@ -77,8 +77,13 @@ typedef enum {
  * refines each tail's coupling columns X_i = K_i^{-1} C_i^T (the nr columns
  * through which the tail meets the root) with the FP32 factor and one
  * float-float residual, forms U_i = C_{i,1} X_i from them, refactors the
- * root, and the solves then use X_i for the root coupling. The flags force
- * one choice. Setting both is BM_ERR_INVALID_ARG.
+ * root, and the solves then use X_i for the root coupling. That indicator
+ * is a heuristic: when a bm_solve's refinement without refined columns
+ * ends BM_ERR_NOT_CONVERGED (stalled or out of steps), the same bm_solve
+ * refines them then, refactors the root, and resumes the refinement from
+ * its last residual with up to max_refine more corrections; later solves on
+ * that factor use the refined columns from the start. The flags force one
+ * choice (and no resumption). Setting both is BM_ERR_INVALID_ARG.
  */
 #define BM_FLAG_COUPLING_REFINE 2u /* always refine the coupling columns */
 #define BM_FLAG_COUPLING_FP32 4u   /* never: R~ from the FP32 tail factor alone */
@@ -103,7 +108,8 @@ typedef struct {
   int fail_stage;      /* BM_ERR_NOT_SPD: 1-based stage k of that tail, 0 for the root */
   int iters;           /* BM_PREC_FP32_IR: refinement steps of the last solve */
   double backward_error; /* BM_PREC_FP32_IR: componentwise backward error of the returned x; FP64: -1 */
-  int coupling_refined;  /* BM_PREC_FP32_IR: 1 if the last bm_factor refined the coupling columns */
+  int coupling_refined;  /* BM_PREC_FP32_IR: 1 if the coupling columns of the last bm_factor are refined
+                            (by that factor, or by a later bm_solve that resumed its refinement) */
   int residual_float_float; /* BM_PREC_FP32_IR: 1 if the refinement residuals of the last bm_solve were
                                float-float, 0 if FP64 (see bm_solve) */
 } bm_info;

@@ -254,7 +254,8 @@ def launches_per_step(S, N, nb, nr, precision=BM_PREC_FP64, max_refine=10, iters
     the refinement). Mixed solve: with
     coupling columns (both modes but BM_FLAG_COUPLING_FP32) one launch for
     the first correction's root terms, then three kernels per refinement
-    iteration; pass the corrections of the solve
+    iteration; in the automatic mode one more, which resumes a failed
+    refinement with refined coupling columns; pass the corrections of the solve
     (``query()["iters"]``) for a captured graph, whose loop stops after the
     last iteration that runs; without it the count is the unrolled
     direct-launch bound (``max_refine <= 0`` selects 10). With float-float
@@ -269,8 +270,14 @@ def launches_per_step(S, N, nb, nr, precision=BM_PREC_FP64, max_refine=10, iters
             return split + (top_level(N) + 2) + 3 * runs
         # refined coupling columns: the first correction's root terms are
         # one more launch per solve (it returns at once when not refined)
-        factor = split + top_level(N) + (6 if flags & BM_FLAG_COUPLING_REFINE else 8)
-        return factor + 1 + 3 * runs
+        if flags & BM_FLAG_COUPLING_REFINE:
+            return split + top_level(N) + 6 + 1 + 3 * runs
+        # automatic: the retry decision after the refinement; launched
+        # directly, also the resumed refinement's launches, which return at
+        # once unless it runs (in a graph they are a conditional node: when
+        # it runs, add 6 + 3 per resumed iteration)
+        retry = 1 if iters is not None else 1 + 6 + 3 * mr
+        return split + top_level(N) + 8 + 1 + 3 * runs + retry
     if nb not in TAIL_NB:
         return (Lc + 2) + (2 * Lc + 3)
     return (top_level(N) + 1) + 3

@@ -35,13 +35,14 @@ cudaError_t mixed_prepare(int nb, int nr);
 MixedState *mixed_create(int S, int N, int nb, int nr, int cmode, int ff, void *base, size_t bytes, Status *status,
                          unsigned *tickets, cudaStream_t init_stream, bool sync_init);
 void mixed_destroy(MixedState *m);
-void mixed_launch_factor(MixedState *m, const double *D, const double *E, const double *C,
-                         const double *R, cudaStream_t st);
+void mixed_launch_factor(MixedState *m, const double *D, const double *E, const double *C, const double *R,
+                         cudaStream_t st);
 // body_st non-null: st is capturing, and the refinement loop becomes a
 // conditional graph node whose body is captured from body_st (programmatic
 // launches inside the body when body_pdl is set).
 cudaError_t mixed_launch_solve(MixedState *m, const double *r, double *x, int max_refine, double tol,
-                               cudaStream_t st, cudaStream_t body_st, bool body_pdl);
+                               cudaStream_t st, cudaStream_t body_st, cudaStream_t if_st, cudaStream_t body2_st,
+                               bool body_pdl);
 void mixed_launch_export(MixedState *m, double *Ld, double *Ll, double *Lr, double *F, double *LR,
                          cudaStream_t st);
 }  // namespace bm
@@ -67,6 +68,8 @@ struct bm_handle_s {
   MixedState *mixed = nullptr;
   cudaStream_t cap = nullptr;      // private capture stream
   cudaStream_t cap_body = nullptr; // captures the body of the refinement loop (mixed path)
+  cudaStream_t cap_if = nullptr;   // automatic mode: the conditional resumed refinement
+  cudaStream_t cap_body2 = nullptr; // and its loop body
   bool loop_pdl = true;            // programmatic launches inside that body (cleared if they do not instantiate)
   GraphSlot gfac, gsol;
   bool factored = false;
@@ -207,7 +210,9 @@ bm_status analyze_impl(const bm_desc *desc, void *mem, size_t bytes, cudaStream_
   }
   if (!light) {
     if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) goto cuda_fail;
-    if (h->mixed && cudaStreamCreateWithFlags(&h->cap_body, cudaStreamNonBlocking) != cudaSuccess)
+    if (h->mixed && (cudaStreamCreateWithFlags(&h->cap_body, cudaStreamNonBlocking) != cudaSuccess ||
+                     cudaStreamCreateWithFlags(&h->cap_if, cudaStreamNonBlocking) != cudaSuccess ||
+                     cudaStreamCreateWithFlags(&h->cap_body2, cudaStreamNonBlocking) != cudaSuccess))
       goto cuda_fail;
     if (cudaDeviceSynchronize() != cudaSuccess) goto cuda_fail;
   }
@@ -218,6 +223,8 @@ cuda_fail:
   if (h->mixed) mixed_destroy(h->mixed);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->cap_body) cudaStreamDestroy(h->cap_body);
+  if (h->cap_if) cudaStreamDestroy(h->cap_if);
+  if (h->cap_body2) cudaStreamDestroy(h->cap_body2);
   if (h->owns_pool) cudaFree(h->pool);
   delete h;
   return BM_ERR_CUDA;
@@ -237,6 +244,8 @@ void release_impl(bm_handle h) {
   if (h->mixed) mixed_destroy(h->mixed);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->cap_body) cudaStreamDestroy(h->cap_body);
+  if (h->cap_if) cudaStreamDestroy(h->cap_if);
+  if (h->cap_body2) cudaStreamDestroy(h->cap_body2);
   if (h->sD) cudaFree(h->sD);
   if (h->owns_pool) cudaFree(h->pool);
   delete h;
@@ -380,7 +389,8 @@ extern "C" bm_status bm_solve(bm_handle h, const double *r, double *x, void *str
     const void *key[6] = {r, x, h->gfac.key[0], h->gfac.key[1], h->gfac.key[2], h->gfac.key[3]};
     cudaStream_t body_st = h->cap_body;
     auto body = [&](cudaStream_t cs, bool capturing) {
-      return mixed_launch_solve(m, r, x, mr, tol, cs, capturing ? body_st : nullptr, h->loop_pdl);
+      return mixed_launch_solve(m, r, x, mr, tol, cs, capturing ? body_st : nullptr, capturing ? h->cap_if : nullptr,
+                                capturing ? h->cap_body2 : nullptr, h->loop_pdl);
     };
     bm_status s = run(h, h->gsol, key, 6, st, body);
     if (s == BM_ERR_CUDA && h->loop_pdl && !(h->desc.flags & BM_FLAG_NO_GRAPH)) {

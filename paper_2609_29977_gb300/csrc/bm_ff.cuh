@@ -78,6 +78,14 @@ __device__ __forceinline__ void split_d(double d, float &hi, float &lo) {
   }
 }
 
+// The float-float residual's range: nonzero magnitudes in [2^-50, 2^50),
+// so that every product of hi and lo parts it forms is a normal float.
+__device__ __forceinline__ bool out_of_range(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d) & 0x7fffffffu, lo = (unsigned)__double2loint(d);
+  const unsigned e = hi >> 20;
+  return (hi | lo) != 0u && (e < 1023u - 50u || e >= 1023u + 50u);
+}
+
 // hi + lo as a double (exact).
 __device__ __forceinline__ double to_double(float hi, float lo) { return f2d_exact(hi) + f2d_exact(lo); }
 

@@ -182,30 +182,46 @@ __global__ void k_widen(const float *__restrict__ src, double *__restrict__ dst,
 
 // K split into hi + lo floats for the float-float residual: D as full
 // symmetric rows (its lower triangle mirrored), E as stored. Sets
-// status->ffbad if a nonzero entry is outside the float-float range.
+// status->ffbad if a nonzero entry is outside the float-float range. D is
+// staged a few blocks at a time in shared memory (read and written
+// contiguously; the mirror is read from shared memory), E streams.
+template <int NB>
+struct SplitCfg {
+  static constexpr int NB2 = NB * NB;
+  static constexpr int BPI = NB2 >= 2048 ? 1 : 2048 / NB2;   // D blocks per staging round
+};
+
 template <int NB>
 __global__ void __launch_bounds__(256) k_ff_split(MixedState m) {
-  constexpr int NB2 = NB * NB;
+  constexpr int NB2 = NB * NB, BPI = SplitCfg<NB>::BPI;
+  __shared__ double sD[BPI * NB2];
   pdl_wait();
-  const long nd = (long)m.S * m.N * NB2, ne = (long)m.S * (m.N - 1) * NB2;
   bool bad = false;
-  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < nd + ne; e += (long)gridDim.x * blockDim.x) {
-    double v;
-    float h, l;
-    if (e < nd) {
-      const long blk = e / NB2;
-      const int w = (int)(e - blk * NB2), i = w / NB, j = w - i * NB;
-      v = j <= i ? m.D[e] : m.D[blk * NB2 + j * NB + i];
+  const long nblk = (long)m.S * m.N;
+  for (long b0 = (long)blockIdx.x * BPI; b0 < nblk; b0 += (long)gridDim.x * BPI) {
+    const int nb = nblk - b0 < BPI ? (int)(nblk - b0) : BPI;
+    const double *src = m.D + b0 * NB2;
+    __syncthreads();
+    for (int e = threadIdx.x; e < nb * NB2; e += blockDim.x) sD[e] = src[e];
+    __syncthreads();
+    for (int e = threadIdx.x; e < nb * NB2; e += blockDim.x) {
+      const int blk = e / NB2, w = e - blk * NB2, i = w / NB, j = w - i * NB;
+      const double v = j <= i ? sD[e] : sD[blk * NB2 + j * NB + i];
+      float h, l;
       ff::split_d(v, h, l);
-      m.Kdh[e] = h;
-      m.Kdl[e] = l;
-    } else {
-      v = m.E[e - nd];
-      ff::split_d(v, h, l);
-      m.Keh[e - nd] = h;
-      m.Kel[e - nd] = l;
+      m.Kdh[b0 * NB2 + e] = h;
+      m.Kdl[b0 * NB2 + e] = l;
+      bad |= ff::out_of_range(v);
     }
-    bad |= ff_out_of_range(v);
+  }
+  const long ne = (long)m.S * (m.N - 1) * NB2;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (long)gridDim.x * blockDim.x) {
+    const double v = m.E[e];
+    float h, l;
+    ff::split_d(v, h, l);
+    m.Keh[e] = h;
+    m.Kel[e] = l;
+    bad |= ff::out_of_range(v);
   }
   if (bad) m.status->ffbad = 1;
   pdl_trigger();
@@ -219,7 +235,7 @@ __global__ void __launch_bounds__(256) k_x_split(MixedState m, const double *__r
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
     const double v = x[e];
     ff::split_d(v, m.xh[e], m.xl[e]);
-    bad |= ff_out_of_range(v);
+    bad |= ff::out_of_range(v);
   }
   if (bad) m.status->ffbad = 1;
 }
@@ -241,6 +257,42 @@ __global__ void __launch_bounds__(256) k_residual_out(MixedState m, const double
       residual_row<NB>(m, r, x, s, k, i);
   }
   for (int c = blockIdx.x; c < m.nr; c += gridDim.x) residual_root_row(m, r, x, NB, c);
+}
+
+// Automatic mode (cmode 1): a refinement that ended BM_ERR_NOT_CONVERGED
+// while the factor's probe had kept the FP32-based root is resumed with
+// refined coupling columns. This kernel decides (one thread): it clears the
+// failure, marks the columns refined for this factor, restarts the
+// iteration count at 1 (the next correction starts from the last residual)
+// and, inside a captured graph, sets the condition of the conditional node
+// that holds the resumed refinement.
+__global__ void k_retry_arm(MixedState m, int max_iter, cudaGraphConditionalHandle cond, int graph) {
+  pdl_wait();
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    IRCtl *c = m.ctl;
+    Status *st = m.status;
+    const bool arm = m.cmode == 1 && max_iter >= 1 && st->code == (int)BM_ERR_NOT_CONVERGED && st->coupled == 0;
+    if (arm) {
+      c->retry = 1;
+      st->coupled = 1;
+      st->code = 0;
+      c->converged = 0;
+      c->wmax = 0u;
+      c->loop = 1;
+      c->omega_prev = __longlong_as_double(0x7ff0000000000000ll);
+    }
+    if (graph) cudaGraphSetConditional(cond, arm ? 1u : 0u);
+  }
+  pdl_trigger();
+}
+
+// Root terms X^T rho of the resumed refinement's first correction (the
+// residual kernel left none: the columns were not refined then).
+template <int NB>
+__global__ void __launch_bounds__(256) k_retry_xt(MixedState m) {
+  pdl_wait();
+  if (*((volatile const int *)&m.ctl->retry)) xt_grid(m, m.rho, NB);
+  pdl_trigger();
 }
 
 int pick_cluster(int S) {
@@ -335,6 +387,63 @@ cudaError_t capture_loop(const MixedState &m, const double *r, double *x, int ma
   cudaGraph_t out = nullptr;
   e = cudaStreamEndCapture(body_st, &out);
   return el != cudaSuccess ? el : e;
+}
+
+// The resumed refinement's launches after the arm kernel: coupling-column
+// refinement and root (both gated by ctl->retry), root terms, then the
+// iterations (a loop node when body_st is set, else max_iter unrolled
+// iterations that return at once unless armed).
+void coupling_launch_cx(const MixedState &m, int *on, cudaStream_t st);
+void retry_root(const MixedState &m, cudaStream_t st);
+
+template <int NB>
+cudaError_t launch_retry_body(const MixedState &m, const double *r, double *x, int max_iter, double tol,
+                              cudaStream_t st, cudaStream_t body_st, bool pdl) {
+  coupling_launch_cx(m, &m.ctl->retry, st);
+  retry_root(m, st);
+  launch_plain(k_retry_xt<NB>, (unsigned)xt_blocks(m.S, m.N, NB, m.nr), 256, 0, true, st, m);
+  if (body_st) return capture_loop<NB>(m, r, x, max_iter, tol, st, body_st, pdl);
+  for (int it = 1; it <= max_iter; ++it) launch_iteration<NB>(m, r, x, it, max_iter, tol, st, 0, true);
+  return cudaPeekAtLastError();
+}
+
+// Captured form: the arm kernel, then a conditional IF node whose body
+// (captured from if_st, its loop body from body_st) is launch_retry_body.
+template <int NB>
+cudaError_t capture_retry(const MixedState &m, const double *r, double *x, int max_iter, double tol,
+                          cudaStream_t st, cudaStream_t if_st, cudaStream_t body_st, bool pdl) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, nullptr, nullptr, nullptr);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusActive || !g) return cudaErrorStreamCaptureInvalidated;
+  cudaGraphConditionalHandle cond = 0;
+  e = cudaGraphConditionalHandleCreate(&cond, g, 0u, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return e;
+  launch_plain(k_retry_arm, 1u, 32, 0, true, st, m, max_iter, cond, 1);
+  const cudaGraphNode_t *deps = nullptr;
+  const cudaGraphEdgeData *edges = nullptr;
+  size_t ndeps = 0;
+  e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &edges, &ndeps);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = cond;
+  p.conditional.type = cudaGraphCondTypeIf;
+  p.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  e = cudaGraphAddNode(&node, g, deps, edges, ndeps, &p);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  e = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamBeginCaptureToGraph(if_st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  const cudaError_t eb = launch_retry_body<NB>(m, r, x, max_iter, tol, if_st, body_st, pdl);
+  const cudaError_t el = cudaPeekAtLastError();
+  cudaGraph_t out = nullptr;
+  e = cudaStreamEndCapture(if_st, &out);
+  return eb != cudaSuccess ? eb : el != cudaSuccess ? el : e;
 }
 
 }  // namespace
@@ -454,6 +563,31 @@ void f64_launch_factor_root_raw(int S, int nr, const double *U, const double *R,
                                 unsigned *tickets, Status *status, int mode, int *on, cudaStream_t st);
 void coupling_launch(const cx::CxView &v, int nb, int *mark, cudaStream_t st);
 
+static cx::CxView cx_view(const MixedState &m, int *on) {
+  cx::CxView cv;
+  cv.S = m.S; cv.N = m.N; cv.nr = m.nr; cv.ldc = m.ldc; cv.Lc = m.Lc;
+  cv.Ld = m.Ld; cv.Ll = m.Ll; cv.Lr = m.Lr; cv.invd = m.invd;
+  cv.D = m.D; cv.E = m.E; cv.C = m.C;
+  cv.Xa = m.Xa; cv.Yb = m.Yb; cv.Zr = m.Zr; cv.U = m.U;
+  cv.on = on;
+  return cv;
+}
+
+static void launch_ff_split(const MixedState &m, cudaStream_t st) {
+  const long n = (long)m.S * (2 * m.N - 1) * m.nb * m.nb;
+  long blocks = (n + 1023) / 1024;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks < 1) blocks = 1;
+  switch (m.nb) {
+#define X(n)                                                            \
+  case n:                                                               \
+    launch_plain(k_ff_split<n>, (unsigned)blocks, 256, 0, true, st, m); \
+    break;
+    BM_TAIL_NB_LIST(X)
+#undef X
+  }
+}
+
 void mixed_launch_factor(MixedState *m, const double *D, const double *E, const double *C, const double *R,
                          cudaStream_t st) {
   m->D = D; m->E = E; m->C = C; m->R = R;
@@ -462,19 +596,8 @@ void mixed_launch_factor(MixedState *m, const double *D, const double *E, const 
   t.D = D; t.E = E; t.C = C; t.R = R;
   t.Ld = m->Ld; t.Ll = m->Ll; t.Lr = m->Lr; t.Dt = m->Dt; t.W = m->W; t.invd = m->invd;
   t.F = m->F; t.U = m->U; t.status = m->status;
-  if (m->ffres) {
-    const long n = (long)m->S * (2 * m->N - 1) * m->nb * m->nb;
-    long blocks = (n + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    switch (m->nb) {
-#define X(n)                                                                       \
-  case n:                                                                          \
-    launch_plain(k_ff_split<n>, (unsigned)blocks, 256, 0, true, st, *m);           \
-    break;
-      BM_TAIL_NB_LIST(X)
-#undef X
-    }
-  }
+  // hi + lo planes of K for the float-float residual
+  if (m->ffres) launch_ff_split(*m, st);
   tail_factor_launch<float>(t, st);
   int *on = &m->status->coupled;
   if (m->cmode == 0) {
@@ -487,19 +610,27 @@ void mixed_launch_factor(MixedState *m, const double *D, const double *E, const 
     launch_plain(k_pivot_spread, (unsigned)m->S, 256, 0, true, st, (const float *)m->invd, m->N, m->nb, m->status);
     f64_launch_factor_root_raw(m->S, m->nr, m->U, R, m->Rt, m->LR, m->tickets, m->status, 1, on, st);
   }
-  cx::CxView cv;
-  cv.S = m->S; cv.N = m->N; cv.nr = m->nr; cv.ldc = m->ldc; cv.Lc = m->Lc;
-  cv.Ld = m->Ld; cv.Ll = m->Ll; cv.Lr = m->Lr; cv.invd = m->invd;
-  cv.D = D; cv.E = E; cv.C = C;
-  cv.Xa = m->Xa; cv.Yb = m->Yb; cv.Zr = m->Zr; cv.U = m->U;
-  cv.on = m->cmode == 1 ? on : nullptr;
+  cx::CxView cv = cx_view(*m, m->cmode == 1 ? on : nullptr);
   coupling_launch(cv, m->nb, m->cmode == 2 ? on : nullptr, st);
   f64_launch_factor_root_raw(m->S, m->nr, m->U, R, m->Rt, m->LR, m->tickets, m->status, m->cmode == 1 ? 2 : 0, on,
                              st);
 }
 
+
+namespace {
+// The coupling-column refinement of the resumed solve, gated by *on.
+void coupling_launch_cx(const MixedState &m, int *on, cudaStream_t st) {
+  coupling_launch(cx_view(m, on), m.nb, nullptr, st);
+}
+// Its root (Alg. 1 steps 4-5 with the refined U_i), gated by ctl->retry.
+void retry_root(const MixedState &m, cudaStream_t st) {
+  f64_launch_factor_root_raw(m.S, m.nr, m.U, m.R, m.Rt, m.LR, m.tickets, m.status, 2, &m.ctl->retry, st);
+}
+}  // namespace
+
 cudaError_t mixed_launch_solve(MixedState *m, const double *r, double *x, int max_refine, double tol,
-                               cudaStream_t st, cudaStream_t body_st, bool body_pdl) {
+                               cudaStream_t st, cudaStream_t body_st, cudaStream_t if_st, cudaStream_t body2_st,
+                               bool body_pdl) {
   // reset the per-solve control words
   cudaError_t e = cudaMemsetAsync(m->ctl, 0, sizeof(IRCtl), st);
   if (e != cudaSuccess) return e;
@@ -513,11 +644,16 @@ cudaError_t mixed_launch_solve(MixedState *m, const double *r, double *x, int ma
 #undef X
     }
   }
+  // automatic mode: a refinement that fails without refined coupling
+  // columns is resumed with them (k_retry_arm)
+  const bool retry = m->cmode == 1;
   if (body_st) {
     switch (m->nb) {
-#define X(n) \
-  case n:    \
-    return capture_loop<n>(*m, r, x, max_refine, tol, st, body_st, body_pdl);
+#define X(n)                                                                                  \
+  case n:                                                                                     \
+    e = capture_loop<n>(*m, r, x, max_refine, tol, st, body_st, body_pdl);                    \
+    if (e == cudaSuccess && retry) e = capture_retry<n>(*m, r, x, max_refine, tol, st, if_st, body2_st, body_pdl); \
+    return e;
       BM_TAIL_NB_LIST(X)
 #undef X
     }
@@ -528,6 +664,17 @@ cudaError_t mixed_launch_solve(MixedState *m, const double *r, double *x, int ma
 #define X(n)                                                     \
   case n:                                                        \
     launch_iteration<n>(*m, r, x, it, max_refine, tol, st, 0, true); \
+    break;
+      BM_TAIL_NB_LIST(X)
+#undef X
+    }
+  }
+  if (retry) {
+    launch_plain(k_retry_arm, 1u, 32, 0, true, st, *m, max_refine, (cudaGraphConditionalHandle)0, 0);
+    switch (m->nb) {
+#define X(n)                                                                        \
+  case n:                                                                           \
+    launch_retry_body<n>(*m, r, x, max_refine, tol, st, nullptr, true);             \
     break;
       BM_TAIL_NB_LIST(X)
 #undef X

@@ -14,6 +14,7 @@ struct IRCtl {
   int loop;                 // index of the next iteration (read by the kernels of a graph loop body)
   double omega_prev;        // omega after the previous iteration
   double eta;               // omega after the last iteration
+  int retry;                // automatic mode: this solve refines the coupling columns and continues
 };
 
 struct MixedState {
@@ -66,14 +67,6 @@ __device__ __forceinline__ float abs_f32_approx(double x) {
   if (e <= 0) return 0.0f;
   if (e >= 255) return __uint_as_float(0x7f7fffffu);
   return __uint_as_float(((unsigned)e << 23) | ((hi & 0xfffffu) << 3));
-}
-
-// The float-float residual's range: nonzero magnitudes in [2^-50, 2^50),
-// so that every product of hi and lo parts it forms is a normal float.
-__device__ __forceinline__ bool ff_out_of_range(double d) {
-  const unsigned hi = (unsigned)__double2hiint(d) & 0x7fffffffu, lo = (unsigned)__double2loint(d);
-  const unsigned e = hi >> 20;
-  return (hi | lo) != 0u && (e < 1023u - 50u || e >= 1023u + 50u);
 }
 
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
@@ -491,7 +484,7 @@ __device__ __forceinline__ void bwd_tail(const MixedState &m, double *x, int ite
           ff::split_d(xv, h, l);
           m.xh[zoff + i] = h;
           m.xl[zoff + i] = l;
-          if (ff_out_of_range(xv)) m.status->ffbad = 1;
+          if (ff::out_of_range(xv)) m.status->ffbad = 1;
         }
       }
       tm.sync();

@@ -12,7 +12,8 @@ coupling of every solve. These tests check, against the FP64 oracle:
     own FP64 residual, forward error bounded by omega times cond(K)),
   * the automatic choice (engaged when the root's cancellation times the
     FP32 factor's pivot spread times 2^-24 exceeds 16, or when the
-    FP32-based root is not positive definite),
+    FP32-based root is not positive definite, or later by the solve when the
+    refinement fails without it),
   * graph and direct launches bit for bit, and repeatability.
 """
 import numpy as np
@@ -139,6 +140,46 @@ def test_automatic_mode_resolves_cancellation_of_1e6():
     assert auto["info"]["coupling_refined"] == 1 and auto["info"]["status"] == 0, auto["info"]
     res = natural.residual(d["D"], d["E"], d["C"], d["R"], auto["x"], d["r"])
     assert res["omega"] <= 2e-10, res
+
+
+RESUME_CASES = [(2, 12, 24, 8, 46, "wishart"), (4, 64, 24, 8, 256, "wishart"), (6, 40, 24, 8, 240, "scaled_identity")]
+
+
+@pytest.mark.parametrize("S,N,nb,nr,seed,root", RESUME_CASES)
+def test_automatic_mode_resumes_a_failed_refinement(S, N, nb, nr, seed, root):
+    """Barrier 10^+-6 systems whose FP32-based root passes the factor's probe
+    (indicator 0.9 to 5) but on which the refinement stalls near 1e-8 with
+    it: the default mode resumes the same solve with refined coupling
+    columns and converges; the next solve on that factor uses them from the
+    start; the graph and direct forms give the same bits; forcing the
+    FP32-based root still reports the stall."""
+    bm = _bm()
+    w = bmgen.Workload("c", S, N, nb, nr, workload_id=94, barrier=(-6.0, 6.0), root=root, shared_A=True)
+    d = bmgen.generate(w, seed=seed)
+    coarse = run(d, flags=bm.BM_FLAG_COUPLING_FP32)
+    assert coarse["info"]["status"] == 5 and coarse["info"]["coupling_refined"] == 0, coarse["info"]
+    outs = []
+    for direct in (False, True):
+        g = {k: (v.cuda() if isinstance(v, torch.Tensor) else v) for k, v in d.items()}
+        solver = bm.BranchKKTSolver(S, N, nb, nr, precision=bm.BM_PREC_FP32_IR, tol=1e-10,
+                                    flags=bm.BM_FLAG_NO_GRAPH if direct else 0)
+        solver.factor(g["D"], g["E"], g["C"], g["R"])
+        x1 = solver.solve(g["r"]).cpu().numpy()
+        i1 = solver.query()
+        x2 = solver.solve(g["r"]).cpu().numpy()
+        i2 = solver.query()
+        solver.close()
+        outs.append((x1, i1, x2, i2))
+        assert i1["status"] == 0 and i1["coupling_refined"] == 1, i1
+        assert i2["status"] == 0 and i2["coupling_refined"] == 1, i2
+        for x in (x1, x2):
+            res = natural.residual(d["D"], d["E"], d["C"], d["R"], x, d["r"])
+            assert res["omega"] <= 1e-10, res["omega"]
+        assert i2["iters"] <= i1["iters"], (i1, i2)
+    (a1, ai1, a2, ai2), (b1, bi1, b2, bi2) = outs
+    assert np.array_equal(a1, b1) and np.array_equal(a2, b2)
+    for k in ("status", "iters", "backward_error"):
+        assert ai1[k] == bi1[k] and ai2[k] == bi2[k], (k, ai1, bi1)
 
 
 def test_unresolvable_cancellation_is_reported():

@@ -98,13 +98,13 @@ def test_float_float_residual_rows_match_exact(S, N, nb, nr):
     assert np.median(np.abs(ex["rho"]) / np.maximum(kx, 1e-300)) < 1e-6, first["info"]
 
 
-@pytest.mark.parametrize("S,N,nb,nr,scale", [(8, 24, 12, 4, 1.0), (6, 40, 24, 8, 3.1e-4), (4, 64, 24, 8, 1.0),
-                                             (3, 17, 16, 5, 1.0)])
-def test_float_float_refinement_meets_tolerance(S, N, nb, nr, scale):
-    """Scale < 1: a root that cancels by about 3e3 / scale, with the coupling
-    columns refined."""
+@pytest.mark.parametrize("S,N,nb,nr,scale,b", [(8, 24, 12, 4, 1.0, 6), (6, 40, 24, 8, 3.1e-4, 4),
+                                               (4, 64, 24, 8, 1.0, 6), (3, 17, 16, 5, 1.0, 6)])
+def test_float_float_refinement_meets_tolerance(S, N, nb, nr, scale, b):
+    """Barrier 10^(+-b); scale < 1: a root that cancels by about 1e3 / scale,
+    with the coupling columns refined."""
     bm = _bm()
-    d = gen(S, N, nb, nr, seed=S * N, root_scale=scale, root="scaled_identity")
+    d = gen(S, N, nb, nr, seed=S * N, barrier=(-b, b), root_scale=scale, root="scaled_identity")
     cf = bm.BM_FLAG_COUPLING_REFINE if scale < 1.0 else 0
     ff = solve(d, tol=1e-10, flags=cf)
     f64 = solve(d, tol=1e-10, flags=cf | bm.BM_FLAG_RESIDUAL_FP64)

@@ -48,12 +48,17 @@ def test_mixed_counts():
                                   flags=core.BM_FLAG_COUPLING_REFINE | core.BM_FLAG_RESIDUAL_FP64) == 10 + 1 + 9
     # automatic (default): pivot-spread reduction and probing root in addition
     assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2,
-                                  flags=core.BM_FLAG_RESIDUAL_FP64) == 12 + 1 + 9
+                                  flags=core.BM_FLAG_RESIDUAL_FP64) == 12 + 1 + 9 + 1
     # float-float residuals (tol >= 1e-11, the default 1e-10): one split launch in the factor
-    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2) == 1 + 12 + 1 + 9
-    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2, tol=1e-11) == 1 + 12 + 1 + 9
-    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2, tol=1e-12) == 12 + 1 + 9
-    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2, tol=0) == 1 + 12 + 1 + 9
+    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2,
+                                  flags=core.BM_FLAG_COUPLING_REFINE) == 1 + 10 + 1 + 9
+    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2) == 1 + 12 + 1 + 9 + 1
+    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2, tol=1e-11) == 1 + 12 + 1 + 9 + 1
+    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2, tol=1e-12) == 12 + 1 + 9 + 1
+    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10, iters=2, tol=0) == 1 + 12 + 1 + 9 + 1
+    # automatic mode launched directly: all 11 iterations, the retry decision,
+    # the resumed refinement's 4 + 1 + 1 launches and its 10 iterations
+    assert core.launches_per_step(64, 64, 12, 4, core.BM_PREC_FP32_IR, 10) == 1 + 12 + 1 + 33 + 1 + 6 + 30
     # the mixed workload (N = 128: levels 0..6, top level 5): 6 tail launches
     assert core.top_level(128) == 5
-    assert core.launches_per_step(512, 128, 24, 8, core.BM_PREC_FP32_IR, 8, iters=3) == 1 + 13 + 1 + 12
+    assert core.launches_per_step(512, 128, 24, 8, core.BM_PREC_FP32_IR, 8, iters=3) == 1 + 13 + 1 + 12 + 1
