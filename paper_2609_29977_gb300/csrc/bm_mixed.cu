@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(256) k_mixed_bwd(MixedState m, double *x, int 
 // of the next correction's root term X^T rho in tb. The last CTA applies
 // the stopping test.
 template <int NB>
-__global__ void __launch_bounds__(256) k_mixed_residual(MixedState m, const double *__restrict__ r,
+__global__ void __launch_bounds__(256, 5) k_mixed_residual(MixedState m, const double *__restrict__ r,
                                                          const double *__restrict__ x, int iter, int max_iter,
                                                          double tol, cudaGraphConditionalHandle cond) {
   __shared__ unsigned sroot;
