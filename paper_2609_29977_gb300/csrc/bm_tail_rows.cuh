@@ -30,6 +30,25 @@ __device__ __forceinline__ T shfl(unsigned mask, T v, int src, int width) {
   return __shfl_sync(mask, v, src, width);
 }
 
+// NB FP64 values addr(0), ..., addr(NB-1) converted to T. Every load of a
+// chunk is issued before its first conversion: the conversion branches on
+// values outside the FP32 normal range, and loads placed after such a
+// branch would each wait for the data of the one before.
+template <typename T, int NB, typename Addr>
+__device__ __forceinline__ void load_to_t(T (&dst)[NB], Addr addr) {
+  constexpr int CH = NB <= 32 ? NB : 16;
+#pragma unroll
+  for (int j0 = 0; j0 < NB; j0 += CH) {
+    double v[CH];
+#pragma unroll
+    for (int t = 0; t < CH; ++t)
+      if (j0 + t < NB) v[t] = addr(j0 + t);
+#pragma unroll
+    for (int t = 0; t < CH; ++t)
+      if (j0 + t < NB) dst[j0 + t] = to_t<T>(v[t]);
+  }
+}
+
 // Copy an NB x NB block (global, type T) into shared memory with the team
 // (row stride Cfg<NB>::LD).
 template <typename T, int NB, int TS>
@@ -117,8 +136,7 @@ __device__ __forceinline__ void factor_task_rows(const TailView<T> &v, T *sX, in
   T d[NB];
   if (lvl <= 1) {
     const double *Dq = v.D + (sb + (N - q)) * NB2;
-#pragma unroll
-    for (int j = 0; j < NB; ++j) d[j] = to_t<T>(j <= ir ? Dq[ir * NB + j] : Dq[j * NB + ir]);
+    load_to_t<T, NB>(d, [&](int j) { return j <= ir ? Dq[ir * NB + j] : Dq[j * NB + ir]; });
   } else {
     const T *Dq = v.Dt + (sb + (N - q)) * NB2 + ir * NB;
 #pragma unroll
@@ -162,8 +180,7 @@ __device__ __forceinline__ void factor_task_rows(const TailView<T> &v, T *sX, in
   T b[NB], av[NB];
   if (lvl == 0 || q == N - 1) {
     const double *Eb = v.E + ((size_t)s * (N - 1) + (N - q - 1)) * NB2;   // M_{b,q} = E^T
-#pragma unroll
-    for (int k = 0; k < NB; ++k) b[k] = to_t<T>(Eb[k * NB + ir]);
+    load_to_t<T, NB>(b, [&](int k) { return Eb[k * NB + ir]; });
   } else {
     const T *Wb = v.W + (sb + (N - q)) * NB2 + ir * NB;
 #pragma unroll
@@ -172,8 +189,7 @@ __device__ __forceinline__ void factor_task_rows(const TailView<T> &v, T *sX, in
   if (hasA) {
     if (lvl == 0) {
       const double *Ea = v.E + ((size_t)s * (N - 1) + (N - q)) * NB2 + ir * NB;
-#pragma unroll
-      for (int k = 0; k < NB; ++k) av[k] = to_t<T>(Ea[k]);
+      load_to_t<T, NB>(av, [&](int k) { return Ea[k]; });
     } else {
       const T *Wa = v.W + (sb + (N - a)) * NB2;   // M_{a,q} = W[a]^T
 #pragma unroll
@@ -241,8 +257,7 @@ __device__ __forceinline__ void x1_task_rows(const TailView<T> &v, void *sbuf, i
   T d[NB];
   if (Lc <= 1) {
     const double *Dq = v.D + sb * NB2;
-#pragma unroll
-    for (int j = 0; j < NB; ++j) d[j] = to_t<T>(j <= ir ? Dq[ir * NB + j] : Dq[j * NB + ir]);
+    load_to_t<T, NB>(d, [&](int j) { return j <= ir ? Dq[ir * NB + j] : Dq[j * NB + ir]; });
   } else {
     const T *Dq = v.Dt + sb * NB2 + ir * NB;
 #pragma unroll
@@ -565,8 +580,7 @@ __device__ __forceinline__ void factor_task_rows_w(const TailView<T> &v, T *sbuf
   T d[NB];
   if (lvl <= 1) {
     const double *Dq = v.D + (sb + (N - q)) * NB2;
-#pragma unroll
-    for (int j = 0; j < NB; ++j) d[j] = to_t<T>(j <= ir ? Dq[ir * NB + j] : Dq[j * NB + ir]);
+    load_to_t<T, NB>(d, [&](int j) { return j <= ir ? Dq[ir * NB + j] : Dq[j * NB + ir]; });
   } else {
     load_row4<T, NB>(d, v.Dt + (sb + (N - q)) * NB2 + ir * NB);
   }
@@ -619,8 +633,7 @@ __device__ __forceinline__ void factor_task_rows_w(const TailView<T> &v, T *sbuf
     T av[NB];
     if (lvl == 0) {
       const double *Ea = v.E + ((size_t)s * (N - 1) + (N - q)) * NB2 + ir * NB;
-#pragma unroll
-      for (int k = 0; k < NB; ++k) av[k] = to_t<T>(Ea[k]);
+      load_to_t<T, NB>(av, [&](int k) { return Ea[k]; });
     } else {
       const T *Wa = v.W + (sb + (N - a)) * NB2;
 #pragma unroll
@@ -642,8 +655,7 @@ __device__ __forceinline__ void factor_task_rows_w(const TailView<T> &v, T *sbuf
   T b[NB];
   if (lvl == 0 || q == N - 1) {
     const double *Eb = v.E + ((size_t)s * (N - 1) + (N - q - 1)) * NB2;
-#pragma unroll
-    for (int k = 0; k < NB; ++k) b[k] = to_t<T>(Eb[k * NB + ir]);
+    load_to_t<T, NB>(b, [&](int k) { return Eb[k * NB + ir]; });
   } else {
     load_row4<T, NB>(b, v.W + (sb + (N - q)) * NB2 + ir * NB);
   }
@@ -680,8 +692,7 @@ __device__ __forceinline__ void x1_task_rows_w(const TailView<T> &v, void *sbuf,
   T d[NB];
   if (Lc <= 1) {
     const double *Dq = v.D + sb * NB2;
-#pragma unroll
-    for (int j = 0; j < NB; ++j) d[j] = to_t<T>(j <= ir ? Dq[ir * NB + j] : Dq[j * NB + ir]);
+    load_to_t<T, NB>(d, [&](int j) { return j <= ir ? Dq[ir * NB + j] : Dq[j * NB + ir]; });
   } else {
     load_row4<T, NB>(d, v.Dt + sb * NB2 + ir * NB);
   }
