@@ -30,12 +30,16 @@ __device__ __forceinline__ T shfl(unsigned mask, T v, int src, int width) {
   return __shfl_sync(mask, v, src, width);
 }
 
-// NB FP64 values addr(0), ..., addr(NB-1) converted to T. Every load of a
-// chunk is issued before its first conversion: the conversion branches on
-// values outside the FP32 normal range, and loads placed after such a
-// branch would each wait for the data of the one before.
+// NB FP64 values addr(0), ..., addr(NB-1) rounded to FP32, every load of a
+// chunk issued before its first conversion. The conversion is the hardware
+// round-to-nearest (on this GPU's FP64 pipe, idle in these FP32 tasks; the
+// same bits as the integer rounding d2f_rn, which a GPU test checks), so
+// that no branch orders the loads: with the integer rounding's
+// out-of-range branch after each value, each load waited for the data of
+// the one before.
 template <typename T, int NB, typename Addr>
 __device__ __forceinline__ void load_to_t(T (&dst)[NB], Addr addr) {
+  static_assert(sizeof(T) == sizeof(float), "FP32 tasks");
   constexpr int CH = NB <= 32 ? NB : 16;
 #pragma unroll
   for (int j0 = 0; j0 < NB; j0 += CH) {
@@ -45,7 +49,7 @@ __device__ __forceinline__ void load_to_t(T (&dst)[NB], Addr addr) {
       if (j0 + t < NB) v[t] = addr(j0 + t);
 #pragma unroll
     for (int t = 0; t < CH; ++t)
-      if (j0 + t < NB) dst[j0 + t] = to_t<T>(v[t]);
+      if (j0 + t < NB) dst[j0 + t] = __double2float_rn(v[t]);
   }
 }
 
