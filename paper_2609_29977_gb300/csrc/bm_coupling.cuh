@@ -294,7 +294,7 @@ __device__ __forceinline__ void bwd_multi(const CxView &v, int s, int crank, int
           mx::load_row<NB>(lrow, v.Ld + (sb + (N - q)) * NB2 + ir * NB);
 #pragma unroll
           for (int c = 0; c < RC; ++c)
-            z[c] = (i < NB && c0 + c < nr) ? d2f_rn(v.C[((size_t)s * nr + c0 + c) * NB + i]) : 0.0f;
+            z[c] = (i < NB && c0 + c < nr) ? __double2float_rn(v.C[((size_t)s * nr + c0 + c) * NB + i]) : 0.0f;
           diag_fwd<NB, TS>(z, lrow, inv, i, tm, sx);
         }
         tm.sync();

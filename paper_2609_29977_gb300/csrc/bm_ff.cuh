@@ -14,8 +14,11 @@
 //    result is as accurate as if computed in twice the working precision
 //    and then rounded;
 //  * split_d: a double as hi + lo floats (hi = the FP32 rounding, lo the
-//    FP32 rounding of d - hi), with integer instructions only, so
-//    |d - hi - lo| <= 2^-48 |d| in the FP32 normal range.
+//    FP32 rounding of d - hi), so |d - hi - lo| <= 2^-48 |d| in the FP32
+//    normal range. hi is the hardware conversion (one FP64-pipe
+//    instruction, branch-free, so that the loads of a loop of splits are
+//    not ordered by a branch); lo comes from the bits with integer
+//    instructions.
 // Every operation is written with the _rn intrinsics so that the compiler
 // neither contracts a product into a later addition nor reorders the sums.
 #pragma once
@@ -56,10 +59,11 @@ __device__ __forceinline__ void dot2_step_split(float &s, float &c, float ah, fl
   c = __fadd_rn(c, __fadd_rn(es, __fmaf_rn(al, b, ep)));
 }
 
-// d = hi + lo (+ at most 2^-48 |d|). Integer instructions and one
-// int-to-float conversion; outside the FP32 normal range lo is 0.
+// d = hi + lo (+ at most 2^-48 |d|). The hardware rounding for hi, integer
+// instructions and one int-to-float conversion for lo; outside the FP32
+// normal range lo is 0.
 __device__ __forceinline__ void split_d(double d, float &hi, float &lo) {
-  hi = d2f_rn(d);
+  hi = __double2float_rn(d);
   const unsigned whi = (unsigned)__double2hiint(d), wlo = (unsigned)__double2loint(d);
   const unsigned e = (whi >> 20) & 0x7ffu;
   lo = 0.0f;

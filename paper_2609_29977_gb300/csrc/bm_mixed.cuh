@@ -267,7 +267,7 @@ __device__ __forceinline__ void fwd_tail(const MixedState &m, const double *__re
       }
       float z = 0.0f;
       if (i < NB) {
-        z = (lvl <= 1) ? d2f_rn(rhs[zoff + i]) : __ldcg(m.zt + zoff + i);
+        z = (lvl <= 1) ? __double2float_rn(rhs[zoff + i]) : __ldcg(m.zt + zoff + i);
         if (lvl >= 1) {
           const int h = 1 << (lvl - 1);
           int pl = 0, pr = 0;
@@ -429,7 +429,7 @@ __device__ __forceinline__ void bwd_tail(const MixedState &m, double *x, int ite
           double zd = f2d_exact(m.y[zoff + i]);
           const double *Fs = m.F + (size_t)s * nr * NB;
           for (int c = 0; c < nr; ++c) zd = fma(-Fs[c * NB + i], __ldcg(m.d0 + c), zd);
-          z = d2f_rn(zd);
+          z = __double2float_rn(zd);
         } else {
           z = m.y[zoff + i];
           const int h = 1 << lvl;
