@@ -68,6 +68,36 @@ __global__ void dmma_k(double* out, int iters) {
 }
 
 
+// Even warps run DFMA chains, odd warps DMMA chains (MODE 0), or only the
+// even (MODE 1) or only the odd ones (MODE 2): if the two share one pipe,
+// MODE 0 takes the sum of the MODE 1 and MODE 2 times; if not, their maximum.
+template <int MODE>
+__global__ void mix_k(double* out, int iters, double a, double b) {
+  const int w = threadIdx.x >> 5;
+  double acc = 0.0;
+  if ((w & 1) == 0) {
+    if (MODE != 2) {
+      double x0=threadIdx.x, x1=x0+1, x2=x0+2, x3=x0+3, x4=x0+4, x5=x0+5, x6=x0+6, x7=x0+7;
+      for (int i = 0; i < iters; ++i) {
+        x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+        x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+      }
+      acc = x0+x1+x2+x3+x4+x5+x6+x7;
+    }
+  } else if (MODE != 1) {
+    double ma = threadIdx.x * 1e-3, mb = 1.0 - threadIdx.x * 1e-4;
+    double c0=0, c1=0, d0=0, d1=0, e0=0, e1=0, f0=0, f1=0;
+    for (int i = 0; i < 2 * iters; ++i) {
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};" : "+d"(c0), "+d"(c1) : "d"(ma), "d"(mb));
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};" : "+d"(d0), "+d"(d1) : "d"(ma), "d"(mb));
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};" : "+d"(e0), "+d"(e1) : "d"(ma), "d"(mb));
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};" : "+d"(f0), "+d"(f1) : "d"(ma), "d"(mb));
+    }
+    acc = c0+c1+d0+d1+e0+e1+f0+f1;
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
 __global__ void dep_chain(double* out, long long* cyc, int iters, double a, double b) {
   double x = threadIdx.x;
   long long t0 = clock64();
@@ -152,6 +182,10 @@ static int part_throughput() {
   run("f2f", [&](int i){ f2f_k<<<blocks, threads>>>(dout, i); }, 4, it, 1.0);
   // dmma: 8x8x4 per warp-instr = 256 FMA = 512 flop per warp; report as lane-ops = 8 FMA per thread per mma
   run("dmma", [&](int i){ dmma_k<<<blocks, threads>>>(dout, i); }, 4 * 8, it / 4, 1.0);
+  // DFMA and DMMA side by side (8 DFMA vs 8 DMMA warp-instructions per warp and iteration)
+  run("mix:dfma+dmma", [&](int i){ mix_k<0><<<blocks, threads>>>(dout, i, 1.0000001, 1e-9); }, 8, it / 4, 1.0);
+  run("mix:dfma only", [&](int i){ mix_k<1><<<blocks, threads>>>(dout, i, 1.0000001, 1e-9); }, 8, it / 4, 1.0);
+  run("mix:dmma only", [&](int i){ mix_k<2><<<blocks, threads>>>(dout, i, 1.0000001, 1e-9); }, 8, it / 4, 1.0);
   CK(cudaGetLastError());
   CK(cudaDeviceSynchronize());
   printf("done\n");
