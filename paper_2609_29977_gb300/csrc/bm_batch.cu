@@ -241,52 +241,43 @@ __device__ void class_worker(const BClass &c, const BInst *inst, const double *c
   }
 }
 
-// Resets the per-factor counters and status words of every system.
-__global__ void k_batch_prep(BInst *inst, int ninst, BClass *cls, int ncls) {
+// Resets the per-factor counters and status words of every system and
+// publishes its inputs for the solves.
+__global__ void k_batch_prep(BInst *inst, int ninst, BClass *cls, int ncls, const double *const *Dp,
+                             const double *const *Ep, const double *const *Cp, const double *const *Rp) {
   const int b = blockIdx.x;
   if (b < ninst) {
-    const BInst &I = inst[b];
+    BInst &I = inst[b];
     for (int s = threadIdx.x; s < I.S; s += blockDim.x) I.tail_done[s] = 0u;
     if (threadIdx.x == 0) {
       *I.x1_done = 0u;
       memset(I.m.status, 0, sizeof(Status));
       for (int k = 0; k < 4; ++k) I.m.tickets[k] = 0u;
+      I.m.D = Dp[b];
+      I.m.E = Ep[b];
+      I.m.C = Cp[b];
+      I.m.R = Rp[b];
     }
   }
   if (b == 0)
     for (int c = threadIdx.x; c < ncls; c += blockDim.x) *cls[c].head = 0ull;
 }
 
-
-__global__ void __launch_bounds__(256) k_batch_factor(const BClass *cls, int ncls, BInst *inst, int ninst,
-                                                      const double *const *Dp, const double *const *Ep,
-                                                      const double *const *Cp, const double *const *Rp,
-                                                      unsigned long long limit) {
+// The queue of one block-size class (cls[c], block size NB) in its own
+// persistent launch: the classes run as parallel branches, each SM mostly
+// holding one class's code, instead of one launch whose CTAs visit every
+// class (and whose SMs then ran the task bodies of all block sizes at once).
+template <int NB>
+__global__ void __launch_bounds__(256) k_batch_factor_nb(const BClass *cls, int c, BInst *inst,
+                                                         const double *const *Dp, const double *const *Ep,
+                                                         const double *const *Cp, const double *const *Rp,
+                                                         unsigned long long limit) {
   extern __shared__ __align__(16) unsigned char smem[];
   pdl_wait();
-  if (blockIdx.x == 0) {
-    // publish the inputs for the solves (read from the handle's table)
-    for (int b = threadIdx.x; b < ninst; b += blockDim.x) {
-      inst[b].m.D = Dp[b];
-      inst[b].m.E = Ep[b];
-      inst[b].m.C = Cp[b];
-      inst[b].m.R = Rp[b];
-    }
-  }
-  const int home = blockIdx.x % ncls;
-  for (int k = 0; k < ncls; ++k) {
-    const BClass &c = cls[(home + k) % ncls];
-    switch (c.nb) {
-#define X(n)                                                         \
-  case n:                                                            \
-    class_worker<n>(c, inst, Dp, Ep, Cp, Rp, smem, limit);           \
-    break;
-      BM_BATCH_NB_LIST(X)
-#undef X
-    }
-    __syncthreads();
-  }
+  class_worker<NB>(cls[c], inst, Dp, Ep, Cp, Rp, smem, limit);
 }
+
+
 
 template <int NB>
 int team_bytes_for(int nr) {
@@ -388,6 +379,8 @@ struct bm_batch_s {
   bool tuned = false, tuned_from_cache = false;
   std::string key;
   cudaStream_t cap = nullptr;
+  cudaStream_t cls_st[8] = {};     // one branch per block-size class
+  cudaEvent_t ev_fork = nullptr, ev_join[8] = {};
   cudaGraphExec_t gfac = nullptr, gsol = nullptr;
   const void *fkey[4] = {nullptr, nullptr, nullptr, nullptr};
   const void *skey[2] = {nullptr, nullptr};
@@ -421,12 +414,41 @@ static size_t smem_for(const bm_batch_s *h, int threads) {
   return best;
 }
 
+static void launch_class(bm_batch_s *h, int c, const double *const *D, const double *const *E,
+                         const double *const *C, const double *const *R, cudaStream_t st, bool pdl) {
+  const unsigned grid = (unsigned)(h->sms * h->ctas_per_sm);
+  const size_t smem = (size_t)(h->threads / team_width(h->cls_nb[c])) * h->cls_team_bytes[c];
+  const unsigned long long limit = 4000000000ull;   // about 2 s of SM clock
+  switch (h->cls_nb[c]) {
+#define X(n)                                                                                                    \
+  case n:                                                                                                       \
+    if (pdl)                                                                                                    \
+      launch_pdl(k_batch_factor_nb<n>, grid, (unsigned)h->threads, smem, st, (const BClass *)h->d_cls, c,      \
+                 h->d_inst, D, E, C, R, limit);                                                                 \
+    else                                                                                                        \
+      k_batch_factor_nb<n><<<grid, h->threads, smem, st>>>(h->d_cls, c, h->d_inst, D, E, C, R, limit);        \
+    break;
+    BM_BATCH_NB_LIST(X)
+#undef X
+  }
+}
+
+// prep, then one persistent launch per block-size class; with more than one
+// class they run as parallel branches (streams forked from and joined to st).
 static void launch_factor(bm_batch_s *h, const double *const *D, const double *const *E, const double *const *C,
                           const double *const *R, cudaStream_t st) {
-  k_batch_prep<<<h->count, 128, 0, st>>>(h->d_inst, h->count, h->d_cls, h->ncls);
-  const unsigned grid = (unsigned)(h->sms * h->ctas_per_sm);
-  launch_pdl(k_batch_factor, grid, (unsigned)h->threads, smem_for(h, h->threads), st, (const BClass *)h->d_cls,
-             h->ncls, h->d_inst, h->count, D, E, C, R, 4000000000ull /* about 2 s of SM clock */);
+  k_batch_prep<<<h->count, 128, 0, st>>>(h->d_inst, h->count, h->d_cls, h->ncls, D, E, C, R);
+  if (h->ncls == 1) {
+    launch_class(h, 0, D, E, C, R, st, true);
+    return;
+  }
+  cudaEventRecord(h->ev_fork, st);
+  for (int c = 0; c < h->ncls; ++c) {
+    cudaStreamWaitEvent(h->cls_st[c], h->ev_fork, 0);
+    launch_class(h, c, D, E, C, R, h->cls_st[c], false);
+    cudaEventRecord(h->ev_join[c], h->cls_st[c]);
+  }
+  for (int c = 0; c < h->ncls; ++c) cudaStreamWaitEvent(st, h->ev_join[c], 0);
 }
 
 static void launch_solve(bm_batch_s *h, const double *const *r, double *const *x, cudaStream_t st) {
@@ -569,9 +591,16 @@ extern "C" bm_status bm_batch_analyze(const bm_desc *descs, int count, void *str
          cudaMemcpy(h->d_cls, cls.data(), cls.size() * sizeof(BClass), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(h->d_segs, segs.data(), segs.size() * sizeof(BSeg), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(h->d_tails, tails.data(), tails.size() * sizeof(BTail), cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaFuncSetAttribute(k_batch_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) ==
-             cudaSuccess &&
-         cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) == cudaSuccess;
+         cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+#define X(n)                                                                                              \
+  ok = ok && cudaFuncSetAttribute(k_batch_factor_nb<n>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+                                  200 * 1024) == cudaSuccess;
+    BM_BATCH_NB_LIST(X)
+#undef X
+    for (int c = 0; ok && c < (int)cls.size(); ++c)
+      ok = cudaStreamCreateWithFlags(&h->cls_st[c], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&h->ev_join[c], cudaEventDisableTiming) == cudaSuccess;
   }
   if (!ok) {
     cudaGetLastError();
@@ -726,6 +755,11 @@ extern "C" void bm_batch_destroy(bm_batch h) {
   if (h->gfac) cudaGraphExecDestroy(h->gfac);
   if (h->gsol) cudaGraphExecDestroy(h->gsol);
   if (h->cap) cudaStreamDestroy(h->cap);
+  for (int c = 0; c < 8; ++c) {
+    if (h->cls_st[c]) cudaStreamDestroy(h->cls_st[c]);
+    if (h->ev_join[c]) cudaEventDestroy(h->ev_join[c]);
+  }
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   cudaFree(h->d_inst);
   cudaFree(h->d_cls);
   cudaFree(h->d_segs);
