@@ -127,8 +127,47 @@ __device__ __forceinline__ void trsm_rows(T (&b)[NB], T (&a)[NB], const T (&lk)[
   }
 }
 
+// chol_rows and trsm_rows fused column by column: each entry L_kj that
+// the Cholesky broadcasts also updates the coupling rows b (and a), which
+// trsm_rows would broadcast a second time, and the inverse pivot 1/L_jj is
+// the r every lane has just computed. The values and the order of the
+// operations on d, b and a are those of chol_rows followed by trsm_rows.
+template <typename T, int NB, int TS, bool TWO>
+__device__ __forceinline__ int chol_trsm_rows(T (&d)[NB], T (&b)[NB], T (&a)[NB], T &rinv, unsigned mask, int i) {
+  int fail = 0;
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    T piv = shfl<T>(mask, d[j], j, TS);
+    if (!pivot_ok(piv)) {
+      if (!fail) fail = j + 1;
+      piv = T(1);
+    }
+    const T r = rsqrt_t<T>(piv);
+    if (i == j) {
+      d[j] = piv * r;
+      rinv = r;
+    } else {
+      d[j] *= r;
+    }
+    b[j] *= r;
+    if (TWO) a[j] *= r;
+#pragma unroll
+    for (int k = j + 1; k < NB; ++k) {
+      const T lkj = shfl<T>(mask, d[j], k, TS);
+      d[k] = fma_t<T>(-d[j], lkj, d[k]);
+      b[k] = fma_t<T>(-b[j], lkj, b[k]);
+      if (TWO) a[k] = fma_t<T>(-a[j], lkj, a[k]);
+    }
+  }
+  return fail;
+}
+
 // One task of level lvl with register-resident rows.
-template <typename T, int NB>
+// FUSED: the Cholesky and the coupling solves in one column loop
+// (chol_trsm_rows; the grid-wide level kernel) or one after the other (the
+// per-tail top kernel and the batched form, whose register budget the
+// fused loop would exceed). Both give the same bits.
+template <typename T, int NB, bool FUSED = false>
 __device__ __forceinline__ void factor_task_rows(const TailView<T> &v, T *sX, int lane, unsigned mask, int s, int q,
                                                  int lvl, bool elim) {
   constexpr int TS = Cfg<NB>::TS, NB2 = NB * NB;
@@ -204,12 +243,19 @@ __device__ __forceinline__ void factor_task_rows(const TailView<T> &v, T *sX, in
     for (int k = 0; k < NB; ++k) av[k] = T(0);
   }
   T rinv = T(1);
-  const int fail = chol_rows<T, NB, TS>(d, rinv, mask, i);
+  int fail;
+  if constexpr (FUSED) {
+    // one instantiation for both cases: without a left neighbour av is zero
+    // and stays +0 through the updates
+    fail = chol_trsm_rows<T, NB, TS, true>(d, b, av, rinv, mask, i);
+  } else {
+    fail = chol_rows<T, NB, TS>(d, rinv, mask, i);
+    if (hasA)
+      trsm_rows<T, NB, TS, true>(b, av, d, rinv, mask);
+    else
+      trsm_rows<T, NB, TS, false>(b, av, d, rinv, mask);
+  }
   if (i == 0 && fail) report_not_spd(v.status, s, N + 1 - q);
-  if (hasA)
-    trsm_rows<T, NB, TS, true>(b, av, d, rinv, mask);
-  else
-    trsm_rows<T, NB, TS, false>(b, av, d, rinv, mask);
   if (act) {
     T *Ld = v.Ld + (sb + (N - q)) * NB2 + i * NB;
     T *Lb = v.Lr + (sb + (N - q)) * NB2 + i * NB;
@@ -358,7 +404,7 @@ __global__ void __launch_bounds__(128, 4) k_level_rows(TailView<T> v, int lvl) {
       q = j < G - 1 ? (j + 1) << (lvl + 1) : N;
       elim = false;
     }
-    factor_task_rows<T, NB>(v, sX, lane, mask, s, q, lvl, elim);
+    factor_task_rows<T, NB, true>(v, sX, lane, mask, s, q, lvl, elim);
   }
   pdl_trigger();
 }
