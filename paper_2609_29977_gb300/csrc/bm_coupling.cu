@@ -16,7 +16,7 @@ namespace {
 using namespace cx;
 
 template <int NB>
-__global__ void __launch_bounds__(256, 2) k_cx_bwd(CxView v, int pass, int CS, int *mark) {
+__global__ void __launch_bounds__(XCfg<NB>::THREADS, XCfg<NB>::MINB) k_cx_bwd(CxView v, int pass, int CS, int *mark) {
   __shared__ __align__(16) float scr[XCfg<NB>::TEAMS * XCfg<NB>::SCR];
   pdl_wait();
   if (engaged(v)) {
@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(256, 2) k_cx_bwd(CxView v, int pass, int CS, i
 }
 
 template <int NB>
-__global__ void __launch_bounds__(256, 2) k_cx_fwd(CxView v, int CS) {
+__global__ void __launch_bounds__(XCfg<NB>::THREADS, XCfg<NB>::MINB) k_cx_fwd(CxView v, int CS) {
   __shared__ __align__(16) float scr[XCfg<NB>::TEAMS * XCfg<NB>::SCR];
   pdl_wait();
   if (engaged(v)) fwd_multi<NB>(v, blockIdx.x / CS, (int)mx::cluster_rank(), CS, scr);
@@ -76,21 +76,23 @@ cudaError_t launch_cx_shape(void (*kern)(KArgs...), unsigned grid, unsigned bloc
 }
 
 template <typename... KArgs, typename... Args>
-cudaError_t launch_cx(void (*kern)(KArgs...), unsigned grid, int CS, cudaStream_t st, Args... args) {
-  return launch_cx_shape(kern, grid, 256, 0, CS, st, args...);
+cudaError_t launch_cx(void (*kern)(KArgs...), unsigned grid, unsigned block, int CS, cudaStream_t st,
+                      Args... args) {
+  return launch_cx_shape(kern, grid, block, 0, CS, st, args...);
 }
 
 template <int NB>
 void launch_nb(const CxView &v, int *mark, cudaStream_t st) {
   const int CS = pick_cluster_cx(v.S);
   const unsigned grid = (unsigned)(v.S * CS);
-  launch_cx(k_cx_bwd<NB>, grid, CS, st, v, 0, CS, mark);
+  constexpr unsigned THR = XCfg<NB>::THREADS;
+  launch_cx(k_cx_bwd<NB>, grid, THR, CS, st, v, 0, CS, mark);
   const long rows = (long)v.S * v.N * NB;
   long blocks = (rows + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
-  launch_cx(k_cx_residual<NB>, (unsigned)blocks, 1, st, v);
-  launch_cx(k_cx_fwd<NB>, grid, CS, st, v, CS);
-  launch_cx(k_cx_bwd<NB>, grid, CS, st, v, 1, CS, (int *)nullptr);
+  launch_cx(k_cx_residual<NB>, (unsigned)blocks, 256u, 1, st, v);
+  launch_cx(k_cx_fwd<NB>, grid, THR, CS, st, v, CS);
+  launch_cx(k_cx_bwd<NB>, grid, THR, CS, st, v, 1, CS, (int *)nullptr);
 }
 
 }  // namespace

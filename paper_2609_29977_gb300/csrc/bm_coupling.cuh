@@ -164,7 +164,12 @@ __device__ __forceinline__ void diag_bwd(float (&z)[RC], const float (&l)[NB], f
 template <int NB>
 struct XCfg {
   static constexpr int TS = mx::MCfg<NB>::TS;
-  static constexpr int TEAMS = mx::MCfg<NB>::TEAMS;
+  // CTAs of four one-warp teams for nb > 16: at up to 128 registers four
+  // such CTAs share an SM, so that the 512 tails of the mixed workload run
+  // in one wave (eight-team CTAs fit two per SM: 1.7 waves)
+  static constexpr int THREADS = TS >= 32 ? 128 : 256;
+  static constexpr int MINB = TS >= 32 ? 4 : 2;
+  static constexpr int TEAMS = THREADS / TS;
   static constexpr int SCR = 3 * NB * RC;   // per-team scratch floats: two neighbours + diagonal exchange
 };
 
