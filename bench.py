@@ -782,6 +782,7 @@ def run_gpu(args):
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
         if code != 0 and not (prec == bm.BM_PREC_FP32_IR and code in (2, 5)):
             raise RuntimeError("host entry status %d" % code)
+    e2e_piped = solver.query().get("host_pipelined", 0)
     e2e_step = max_over_ranks(statistics.mean(e2e_ms), dist, dev)
     h2d = sum(pin[k].numel() * 8 for k in ("D", "E", "C", "R", "r"))
     d2h = xh.numel() * 8
@@ -856,7 +857,8 @@ def run_gpu(args):
                      "achieved_basis": "method flops of one factor (%.4g) / mean factor time over the timed "
                                        "steps (CUDA events on the launching stream)" % fl["factor"]},
         "e2e": {"value": whole_job_gflops(world, fl["total"], 1, e2e_step), "unit": "GFLOP/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step,
+                "copies_overlap_factor": bool(e2e_piped)},
         "gpu_launches": launches_per_step * args.steps,
         "schedule": _schedule_of(solver, bm),
         "clocks": clocks,

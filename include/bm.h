@@ -112,6 +112,8 @@ typedef struct {
                             (by that factor, or by a later bm_solve that resumed its refinement) */
   int residual_float_float; /* BM_PREC_FP32_IR: 1 if the refinement residuals of the last bm_solve were
                                float-float, 0 if FP64 (see bm_solve) */
+  int host_pipelined;  /* BM_PREC_FP64: 1 if the last bm_factor_solve_host overlapped its input copies
+                          with the factor (see bm_factor_solve_host), else 0 */
 } bm_info;
 
 /* Library version (BM_VERSION). */
@@ -241,8 +243,16 @@ bm_status bm_export_factor(bm_handle h, double *Ld, double *Ll, double *Lr, doub
  * copies hD, hE, hC, hR, hr to device buffers owned by the handle
  * (allocated on first use), runs bm_factor and bm_solve, copies x back to
  * hx, and synchronizes stream before returning (hx is valid on return).
- * Pinned (page-locked) host buffers give asynchronous copies.
- * Returns the sticky device status like bm_query.
+ * Pinned (page-locked) host buffers give asynchronous copies. For
+ * BM_PREC_FP64 handles whose nb has compiled tail kernels, with page-locked
+ * inputs and S >= 2, every call after the first (which chooses the launch
+ * schedule) overlaps the copies with the factor: the tails' blocks move in
+ * up to 8 chunks on a second stream, and the first two grid-wide levels of
+ * Alg. 1 step 1 run on each chunk as soon as it has arrived (the tails are
+ * independent until the root reduction); the other levels, the root step
+ * and the solve follow once all inputs are on the device. The result is
+ * bitwise that of bm_factor + bm_solve on the same data; bm_info reports
+ * which form ran. Returns the sticky device status like bm_query.
  */
 bm_status bm_factor_solve_host(bm_handle h, const double *hD, const double *hE,
                                const double *hC, const double *hR, const double *hr,

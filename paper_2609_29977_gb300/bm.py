@@ -50,7 +50,7 @@ class bm_desc(ctypes.Structure):
 class bm_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("fail_scenario", ctypes.c_int), ("fail_stage", ctypes.c_int),
                 ("iters", ctypes.c_int), ("backward_error", ctypes.c_double), ("coupling_refined", ctypes.c_int),
-                ("residual_float_float", ctypes.c_int)]
+                ("residual_float_float", ctypes.c_int), ("host_pipelined", ctypes.c_int)]
 
 
 class bm_qp_desc(ctypes.Structure):
@@ -317,7 +317,7 @@ def bm_query(h, stream=None) -> dict:
     return {"status": int(code), "name": STATUS_NAMES.get(int(code), str(code)),
             "fail_scenario": info.fail_scenario, "fail_stage": info.fail_stage, "iters": info.iters,
             "backward_error": info.backward_error, "coupling_refined": int(info.coupling_refined),
-            "residual_float_float": int(info.residual_float_float)}
+            "residual_float_float": int(info.residual_float_float), "host_pipelined": int(info.host_pipelined)}
 
 
 def bm_schedule(h) -> dict:

@@ -24,6 +24,8 @@ bool tune_cache_lookup(const std::string &key, std::vector<int> &vals);
 void tune_cache_store(const std::string &key, const std::vector<int> &vals);
 void f64_launch_solve(const F64View &v, const double *r, double *x, double *r0t, cudaStream_t st);
 void f64_launch_export_ld(const F64View &v, double *Ld, cudaStream_t st);
+void f64_launch_factor_part(const F64View &v, int s0, int s1, int lo, int hi, bool top, cudaStream_t st,
+                            const TailSched *sc);
 
 // mixed precision path (bm_mixed.cu)
 struct MixedState;
@@ -48,6 +50,10 @@ void mixed_launch_export(MixedState *m, double *Ld, double *Ll, double *Lr, doub
 }  // namespace bm
 
 using namespace bm;
+
+// Chunks of tails whose host-to-device copies the pipelined host entry
+// overlaps with the factor.
+static constexpr int kHostChunks = 8;
 
 struct GraphSlot {
   cudaGraphExec_t exec = nullptr;
@@ -80,6 +86,13 @@ struct bm_handle_s {
   bool sched_ready = false;
   // host-entry staging (allocated on first use)
   double *sD = nullptr, *sE = nullptr, *sC = nullptr, *sR = nullptr, *sr = nullptr, *sx = nullptr;
+  // pipelined host entry (FP64): copy stream, its events (fork, one per
+  // chunk of tails, the rest of the inputs) and the captured factor
+  cudaStream_t cp_st = nullptr;
+  cudaEvent_t ev_cp[kHostChunks + 2] = {};
+  bool pipe_failed = false;
+  bool pipe_last = false;   // the last host-entry call was pipelined
+  GraphSlot ghost;
 };
 
 static bool valid_desc(const bm_desc *d) {
@@ -241,6 +254,10 @@ void release_impl(bm_handle h) {
   if (!h) return;
   if (h->gfac.exec) cudaGraphExecDestroy(h->gfac.exec);
   if (h->gsol.exec) cudaGraphExecDestroy(h->gsol.exec);
+  if (h->ghost.exec) cudaGraphExecDestroy(h->ghost.exec);
+  for (cudaEvent_t ev : h->ev_cp)
+    if (ev) cudaEventDestroy(ev);
+  if (h->cp_st) cudaStreamDestroy(h->cp_st);
   if (h->mixed) mixed_destroy(h->mixed);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->cap_body) cudaStreamDestroy(h->cap_body);
@@ -446,6 +463,7 @@ extern "C" bm_status bm_query(bm_handle h, void *stream, bm_info *info) {
     info->backward_error = h->mixed ? st.eta : -1.0;
     info->coupling_refined = h->mixed ? st.coupled : 0;
     info->residual_float_float = h->mixed && mixed_ffres(h->mixed) && !st.ffbad ? 1 : 0;
+    info->host_pipelined = h->pipe_last ? 1 : 0;
   }
   return (bm_status)st.code;
 }
@@ -475,6 +493,93 @@ extern "C" bm_status bm_export_factor(bm_handle h, double *Ld, double *Ll, doubl
   return e == cudaSuccess ? BM_OK : BM_ERR_CUDA;
 }
 
+static bool host_pinned(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
+// The factor of the host entry with its copies pipelined (FP64 tails with
+// compile-time kernels, a schedule already chosen, page-locked inputs): the
+// tails' blocks are copied in kHostChunks chunks on a second stream, and the
+// first two grid-wide levels of a chunk run as soon as its blocks have
+// arrived, so the transfer of later chunks overlaps the factor of earlier
+// ones. The remaining levels and the top kernel (whose last CTA does the
+// root step) run over all tails once every input has arrived. Every block
+// is computed by the same kernels in the same order as in bm_factor, so the
+// factor is bitwise that of the device entry. Returns false when the
+// pipelined form does not apply or could not be issued; the caller then
+// copies and factors serially.
+static bool factor_host_pipelined(bm_handle h, const double *hD, const double *hE, const double *hC,
+                                  const double *hR, const double *hr, cudaStream_t st, bm_status *out) {
+  const bm_desc &d = h->desc;
+  if (h->mixed || h->pipe_failed || !h->sched_ready || !tail_nb_supported(d.nb) || d.S < 2) return false;
+  if (!h->cap && !(d.flags & BM_FLAG_NO_GRAPH)) return false;
+  if (!host_pinned(hD) || !host_pinned(hC) || !host_pinned(hR) || !host_pinned(hr) ||
+      (d.N > 1 && !host_pinned(hE)))
+    return false;
+  if (!h->cp_st) {
+    bool ok = cudaStreamCreateWithFlags(&h->cp_st, cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; ok && i < kHostChunks + 2; ++i)
+      ok = cudaEventCreateWithFlags(&h->ev_cp[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      h->pipe_failed = true;
+      return false;
+    }
+  }
+  const int S = d.S, N = d.N, nb = d.nb, nr = d.nr;
+  const size_t b2 = (size_t)nb * nb, n = (size_t)S * N * nb + nr;
+  const int K = S < kHostChunks ? S : kHostChunks;
+  const int lp = h->sched.top < 2 ? h->sched.top : 2;
+  F64View v = h->v;
+  v.D = h->sD; v.E = N > 1 ? h->sE : nullptr; v.C = h->sC; v.R = h->sR;
+  const TailSched *sc = &h->sched;
+  const cudaMemcpyKind H2D = cudaMemcpyHostToDevice;
+  const void *key[5] = {hD, hE, hC, hR, hr};
+  *out = run(h, h->ghost, key, 5, st, [&](cudaStream_t cs, bool) -> cudaError_t {
+    cudaStream_t cp = h->cp_st;
+    cudaError_t e = cudaMemsetAsync(v.status, 0, sizeof(Status), cs);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_cp[0], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cp, h->ev_cp[0], 0);
+    for (int c = 0; c < K && e == cudaSuccess; ++c) {
+      const size_t s0 = (size_t)S * c / K, s1 = (size_t)S * (c + 1) / K;
+      e = cudaMemcpyAsync(h->sD + s0 * N * b2, hD + s0 * N * b2, (s1 - s0) * N * b2 * 8, H2D, cp);
+      if (e == cudaSuccess && N > 1)
+        e = cudaMemcpyAsync(h->sE + s0 * (N - 1) * b2, hE + s0 * (N - 1) * b2, (s1 - s0) * (N - 1) * b2 * 8, H2D,
+                            cp);
+      if (e == cudaSuccess) e = cudaEventRecord(h->ev_cp[1 + c], cp);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->sC, hC, (size_t)S * nr * nb * 8, H2D, cp);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->sR, hR, (size_t)nr * nr * 8, H2D, cp);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->sr, hr, n * 8, H2D, cp);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_cp[K + 1], cp);
+    for (int c = 0; c < K && e == cudaSuccess; ++c) {
+      e = cudaStreamWaitEvent(cs, h->ev_cp[1 + c], 0);
+      if (e == cudaSuccess && lp > 0)
+        f64_launch_factor_part(v, (int)((long)S * c / K), (int)((long)S * (c + 1) / K), 0, lp, false, cs, sc);
+    }
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, h->ev_cp[K + 1], 0);
+    if (e == cudaSuccess) f64_launch_factor_part(v, 0, S, lp, 1 << 30, true, cs, sc);
+    return e == cudaSuccess ? cudaPeekAtLastError() : e;
+  });
+  if (*out != BM_OK) {
+    // a form that cannot be captured or launched here is not tried again:
+    // once the copy stream is idle, this call and later ones take the
+    // serial form
+    h->pipe_failed = true;
+    cudaStreamSynchronize(h->cp_st);
+    cudaGetLastError();
+    return false;
+  }
+  h->v.D = v.D; h->v.E = v.E; h->v.C = v.C; h->v.R = v.R;
+  h->factored = true;
+  return true;
+}
+
 extern "C" bm_status bm_factor_solve_host(bm_handle h, const double *hD, const double *hE, const double *hC,
                                           const double *hR, const double *hr, double *hx, void *stream) {
   if (!h || !hD || !hC || !hR || !hr || !hx || (h->desc.N > 1 && !hE)) return BM_ERR_INVALID_ARG;
@@ -498,16 +603,20 @@ extern "C" bm_status bm_factor_solve_host(bm_handle h, const double *hD, const d
     h->sx = (double *)c;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = cudaMemcpyAsync(h->sD, hD, nD * 8, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && nE) e = cudaMemcpyAsync(h->sE, hE, nE * 8, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h->sC, hC, nC * 8, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h->sR, hR, nR * 8, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h->sr, hr, n * 8, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return BM_ERR_CUDA;
+  bm_status s = BM_OK;
+  h->pipe_last = factor_host_pipelined(h, hD, hE, hC, hR, hr, st, &s);
+  if (!h->pipe_last) {
+    cudaError_t e = cudaMemcpyAsync(h->sD, hD, nD * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && nE) e = cudaMemcpyAsync(h->sE, hE, nE * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->sC, hC, nC * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->sR, hR, nR * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->sr, hr, n * 8, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return BM_ERR_CUDA;
+    }
+    s = bm_factor(h, h->sD, nE ? h->sE : nullptr, h->sC, h->sR, stream);
   }
-  bm_status s = bm_factor(h, h->sD, nE ? h->sE : nullptr, h->sC, h->sR, stream);
   if (s != BM_OK) return s;
   s = bm_solve(h, h->sr, h->sx, stream);
   if (s != BM_OK) return s;

@@ -735,6 +735,8 @@ extern "C" bm_status bm_batch_query(bm_batch h, void *stream, bm_info *infos) {
       infos[b].iters = st[b].iters;
       infos[b].backward_error = st[b].eta;
       infos[b].coupling_refined = 0;
+      infos[b].residual_float_float = 0;
+      infos[b].host_pipelined = 0;
     }
     if (first == BM_OK && st[b].code != 0) first = (bm_status)st[b].code;
   }

@@ -496,6 +496,28 @@ bool f64_tune(const F64View &v, cudaStream_t st, TailSched *out) {
   return tail_factor_tune(tail_view_of(v), st, out);
 }
 
+// Part of the FP64 factor for pipelined callers (block sizes with
+// compile-time kernels): the grid-wide levels [lo, hi) of tails [s0, s1)
+// and, if top, the top kernel over those tails; its last CTA does the root
+// step only when the range holds every tail.
+void f64_launch_factor_part(const F64View &v, int s0, int s1, int lo, int hi, bool top, cudaStream_t st,
+                            const TailSched *sc) {
+  TailView<double> t = tail_view_of(v);
+  const size_t o = (size_t)s0 * v.N, b2 = (size_t)v.nb * v.nb;
+  t.S = s1 - s0;
+  t.s0 = s0;
+  t.D = v.D + o * b2;
+  t.E = v.E ? v.E + (size_t)s0 * (v.N - 1) * b2 : nullptr;
+  t.C = v.C + (size_t)s0 * v.nr * v.nb;
+  t.Ld = v.Ld + o * b2; t.Ll = v.Ll + o * b2; t.Lr = v.Lr + o * b2;
+  t.Dt = v.Dt + o * b2; t.W = v.W + o * b2;
+  t.invd = v.invd + o * v.nb;
+  t.F = v.F + (size_t)s0 * v.nr * v.nb;
+  t.U = v.U + (size_t)s0 * v.nr * v.nr;
+  if (s0 != 0 || s1 != v.S) t.LR = nullptr;
+  tail_factor_launch_range(t, st, sc, lo, hi, top);
+}
+
 void f64_launch_factor(const F64View &v, cudaStream_t st, const TailSched *sc) {
   if (tail_nb_supported(v.nb)) {
     // the top kernel's last CTA finishes with the root step

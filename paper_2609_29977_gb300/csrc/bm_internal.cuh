@@ -149,6 +149,9 @@ struct TailView {
   // when LR is set (ticket tickets[0]); null elsewhere
   double *Rt, *LR;
   unsigned *tickets;
+  // index of this view's first tail among all tails of the system (a view
+  // over a range of tails reports failures with system-wide indices)
+  int s0;
 };
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -186,6 +189,8 @@ void tail_factor_launch(const TailView<T> &v, cudaStream_t st, const TailSched *
                         cudaEvent_t *ev = nullptr);
 // The default schedule, and the autotuned one (times candidate team sizes
 // per level and top levels on the given inputs, synchronizing st).
+void tail_factor_launch_range(const TailView<double> &v, cudaStream_t st, const TailSched *sc, int lo, int hi,
+                              bool top);
 void tail_default_schedule(int S, int N, int nb, TailSched *sc);
 bool tail_factor_tune(const TailView<double> &v, cudaStream_t st, TailSched *best);
 

@@ -13,6 +13,8 @@ namespace tail {
                                                  cudaEvent_t *);                                           \
   extern template void launch_tail_nb<float, n>(const TailView<float> &, cudaStream_t, const TailSched *,   \
                                                 cudaEvent_t *);                                            \
+  extern template void launch_tail_range<double, n>(const TailView<double> &, cudaStream_t, const TailSched *, \
+                                                    int, int, bool, cudaEvent_t *);                            \
   extern template cudaError_t prepare_nb<double, n>();                              \
   extern template cudaError_t prepare_nb<float, n>();
 BM_TAIL_NB_LIST(X)
@@ -88,6 +90,20 @@ void tail_factor_launch(const TailView<T> &v, cudaStream_t st, const TailSched *
 }
 template void tail_factor_launch<double>(const TailView<double> &, cudaStream_t, const TailSched *, cudaEvent_t *);
 template void tail_factor_launch<float>(const TailView<float> &, cudaStream_t, const TailSched *, cudaEvent_t *);
+
+// FP64 tails: grid-wide levels [lo, hi) of the tails in v, then the top
+// kernel if top (a part of the factor, for pipelined callers).
+void tail_factor_launch_range(const TailView<double> &v, cudaStream_t st, const TailSched *sc, int lo, int hi,
+                              bool top) {
+  switch (v.nb) {
+#define X(n)                                                        \
+  case n:                                                           \
+    tail::launch_tail_range<double, n>(v, st, sc, lo, hi, top, nullptr); \
+    break;
+    BM_TAIL_NB_LIST(X)
+#undef X
+  }
+}
 
 void tail_default_schedule(int S, int N, int nb, TailSched *sc) {
   sc->top = top_level(N);

@@ -102,7 +102,7 @@ __device__ __forceinline__ void factor_task(const TailView<T> &v, const Team<TEA
   }
   tm.sync();
   const int fail = team_chol<TEAM, NB, T>(tm, sD, sInv);
-  if (tm.lane == 0 && fail) report_not_spd(v.status, s, N + 1 - q);
+  if (tm.lane == 0 && fail) report_not_spd(v.status, v.s0 + s, N + 1 - q);
   team_store_factor<TEAM, NB, T>(tm, v.Ld + (sb + (N - q)) * NB2, sD, sInv);
   team_trsm_lt<TEAM, NB, T>(tm, sB, hasA ? 2 * NB : NB, sD, sInv);
   team_copy<TEAM, NB2>(tm, v.Lr + (sb + (N - q)) * NB2, sB);
@@ -146,7 +146,7 @@ __device__ __forceinline__ void x1_task(const TailView<T> &v, const Team<TEAM> &
     tm.sync();
   }
   const int fail = team_chol<TEAM, NB, T>(tm, sD, sInv);
-  if (tm.lane == 0 && fail) report_not_spd(v.status, s, 1);
+  if (tm.lane == 0 && fail) report_not_spd(v.status, v.s0 + s, 1);
   team_store_factor<TEAM, NB, T>(tm, v.Ld + sb * NB2, sD, sInv);
   team_zero<TEAM, NB2>(tm, v.Ll + sb * NB2);
   team_zero<TEAM, NB2>(tm, v.Lr + sb * NB2);
@@ -317,11 +317,15 @@ void launch_level_clamped(const TailView<T> &v, int lvl, long tasks, cudaStream_
   launch_level<T, NB, t>(v, lvl, tasks, st);
 }
 
+// Grid-wide levels [lo, min(hi, top)) of the tails in v and, if top, the
+// per-tail top kernel. With ev, ev[l] is recorded before level l and ev[top+1]
+// after the top kernel.
 template <typename T, int NB>
-void launch_tail_nb(const TailView<T> &v, cudaStream_t st, const TailSched *sc, cudaEvent_t *ev) {
+void launch_tail_range(const TailView<T> &v, cudaStream_t st, const TailSched *sc, int lo, int hi, bool top,
+                       cudaEvent_t *ev) {
   const int Tl = sc ? sc->top : top_level(v.N);
   if (ev) cudaEventRecord(ev[0], st);
-  for (int l = 0; l < Tl; ++l) {
+  for (int l = lo; l < Tl && l < hi; ++l) {
     const int E = level_elims(v.N, l);
     const int G = l == 0 ? 0 : ((v.N - 1) >> (l + 1)) + 1;
     const long tasks = (long)v.S * (E + G);
@@ -334,8 +338,14 @@ void launch_tail_nb(const TailView<T> &v, cudaStream_t st, const TailSched *sc, 
     }
     if (ev) cudaEventRecord(ev[l + 1], st);
   }
+  if (!top) return;
   launch_top<T, NB, team_top(NB)>(v, Tl, st);
   if (ev) cudaEventRecord(ev[Tl + 1], st);
+}
+
+template <typename T, int NB>
+void launch_tail_nb(const TailView<T> &v, cudaStream_t st, const TailSched *sc, cudaEvent_t *ev) {
+  launch_tail_range<T, NB>(v, st, sc, 0, 1 << 30, true, ev);
 }
 
 }  // namespace tail

@@ -4,8 +4,12 @@
 namespace bm {
 namespace tail {
 template void launch_tail_nb<double, 24>(const TailView<double> &, cudaStream_t, const TailSched *, cudaEvent_t *);
+template void launch_tail_range<double, 24>(const TailView<double> &, cudaStream_t, const TailSched *, int, int,
+                                             bool, cudaEvent_t *);
 template cudaError_t prepare_nb<double, 24>();
 template void launch_tail_nb<double, 32>(const TailView<double> &, cudaStream_t, const TailSched *, cudaEvent_t *);
+template void launch_tail_range<double, 32>(const TailView<double> &, cudaStream_t, const TailSched *, int, int,
+                                             bool, cudaEvent_t *);
 template cudaError_t prepare_nb<double, 32>();
 }  // namespace tail
 }  // namespace bm

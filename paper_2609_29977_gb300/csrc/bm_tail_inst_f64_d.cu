@@ -4,6 +4,8 @@
 namespace bm {
 namespace tail {
 template void launch_tail_nb<double, 48>(const TailView<double> &, cudaStream_t, const TailSched *, cudaEvent_t *);
+template void launch_tail_range<double, 48>(const TailView<double> &, cudaStream_t, const TailSched *, int, int,
+                                             bool, cudaEvent_t *);
 template cudaError_t prepare_nb<double, 48>();
 }  // namespace tail
 }  // namespace bm

@@ -208,16 +208,68 @@ def test_fp64_repeat_is_deterministic_and_reuses_factor():
     solver.close()
 
 
-def test_fp64_host_entry_matches_device_entry():
+# (S, N, nb, nr, pipelined): nb = 5 has no compiled tail kernels (serial
+# copies); the others overlap the copies of later chunks of tails with the
+# first levels of earlier ones from the second call on (S = 3: one tail per
+# chunk; S = 12: uneven chunks; N = 64: two levels per chunk; N = 2: none)
+HOST_CASES = [(3, 11, 5, 2, False), (3, 16, 4, 2, True), (12, 64, 4, 2, True), (19, 33, 12, 3, True),
+              (9, 2, 6, 3, True)]
+
+
+@pytest.mark.parametrize("S,N,nb,nr,piped", HOST_CASES)
+def test_fp64_host_entry_matches_device_entry(S, N, nb, nr, piped):
     bm = _bm()
-    d = gen(3, 11, 5, 2, seed=13)
+    d = gen(S, N, nb, nr, seed=13)
     dev = run_gpu(d)
-    solver = bm.BranchKKTSolver(3, 11, 5, 2)
+    solver = bm.BranchKKTSolver(S, N, nb, nr)
     pin = {k: d[k].contiguous().pin_memory() for k in ("D", "E", "C", "R", "r")}
     x = torch.empty_like(pin["r"]).pin_memory()
-    x, code = solver.factor_solve_host(pin["D"], pin["E"], pin["C"], pin["R"], pin["r"], x)
+    for call in range(3):
+        x.fill_(float("nan"))
+        x, code = solver.factor_solve_host(pin["D"], pin["E"], pin["C"], pin["R"], pin["r"], x)
+        assert code == 0
+        assert solver.query()["host_pipelined"] == (1 if piped and call > 0 else 0)
+        assert np.array_equal(x.numpy(), dev["x"])
+    # pageable inputs take the serial copies, with the same result
+    page = {k: d[k].contiguous().clone() for k in ("D", "E", "C", "R", "r")}
+    xp = torch.empty_like(page["r"])
+    xp, code = solver.factor_solve_host(page["D"], page["E"], page["C"], page["R"], page["r"], xp)
+    assert code == 0 and solver.query()["host_pipelined"] == 0
+    assert np.array_equal(xp.numpy(), dev["x"])
+    solver.close()
+
+
+@pytest.mark.parametrize("scenario,stage", [(8, 2), (8, 3), (11, 57), (0, 1), (7, 64)])
+def test_fp64_host_entry_pipelined_reports_location(scenario, stage):
+    """A non-SPD block in a later chunk of tails is reported with the
+    system-wide scenario index by the pipelined host entry (chunks of S = 12
+    tails: [0,1) [1,3) [3,4) [4,6) [6,7) [7,9) [9,10) [10,12)); stages 2 and
+    64 are eliminated at level 0, 3 at level 1 (both run per chunk), 57 at
+    level 3 (the top kernel) and 1 is x_1."""
+    bm = _bm()
+    d = gen(12, 64, 4, 2, seed=5)
+    pin = {k: d[k].contiguous().pin_memory() for k in ("D", "E", "C", "R", "r")}
+    bad = d["D"].clone()
+    bad[scenario, stage - 1] = -torch.eye(4, dtype=torch.float64)
+    bad = bad.contiguous().pin_memory()
+    solver = bm.BranchKKTSolver(12, 64, 4, 2, flags=bm.BM_FLAG_NO_TUNE)   # default schedule: top level 3
+    x = torch.empty_like(pin["r"]).pin_memory()
+    _, code = solver.factor_solve_host(pin["D"], pin["E"], pin["C"], pin["R"], pin["r"], x)
     assert code == 0
-    assert np.array_equal(x.numpy(), dev["x"])
+    _, code = solver.factor_solve_host(bad, pin["E"], pin["C"], pin["R"], pin["r"], x)
+    info = solver.query()
+    assert info["host_pipelined"] == 1
+    assert code == 2 and info["fail_scenario"] == scenario and info["fail_stage"] == stage, info
+    # the same location as the device entry
+    g = to_dev(d)
+    ref = bm.BranchKKTSolver(12, 64, 4, 2)
+    ref.factor(bad.cuda(), g["E"], g["C"], g["R"])
+    rinfo = ref.query()
+    assert (rinfo["fail_scenario"], rinfo["fail_stage"]) == (scenario, stage)
+    ref.close()
+    # the status is cleared by the next call
+    _, code = solver.factor_solve_host(pin["D"], pin["E"], pin["C"], pin["R"], pin["r"], x)
+    assert code == 0 and solver.query()["host_pipelined"] == 1
     solver.close()
 
 
