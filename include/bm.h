@@ -247,8 +247,8 @@ bm_status bm_export_factor(bm_handle h, double *Ld, double *Ll, double *Lr, doub
  * BM_PREC_FP64 handles whose nb has compiled tail kernels, with page-locked
  * inputs and S >= 2, every call after the first (which chooses the launch
  * schedule) overlaps the copies with the factor: the tails' blocks move in
- * up to 8 chunks on a second stream, and the first two grid-wide levels of
- * Alg. 1 step 1 run on each chunk as soon as it has arrived (the tails are
+ * up to 8 chunks on a second stream, and the first odd-even level of Alg. 1
+ * step 1 runs on each chunk as soon as it has arrived (the tails are
  * independent until the root reduction); the other levels, the root step
  * and the solve follow once all inputs are on the device. The result is
  * bitwise that of bm_factor + bm_solve on the same data; bm_info reports

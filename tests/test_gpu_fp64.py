@@ -210,8 +210,8 @@ def test_fp64_repeat_is_deterministic_and_reuses_factor():
 
 # (S, N, nb, nr, pipelined): nb = 5 has no compiled tail kernels (serial
 # copies); the others overlap the copies of later chunks of tails with the
-# first levels of earlier ones from the second call on (S = 3: one tail per
-# chunk; S = 12: uneven chunks; N = 64: two levels per chunk; N = 2: none)
+# first level of earlier ones from the second call on (S = 3: one tail per
+# chunk; S = 12 and 19: uneven chunks; N = 2: no level before the top kernel)
 HOST_CASES = [(3, 11, 5, 2, False), (3, 16, 4, 2, True), (12, 64, 4, 2, True), (19, 33, 12, 3, True),
               (9, 2, 6, 3, True)]
 
@@ -244,8 +244,8 @@ def test_fp64_host_entry_pipelined_reports_location(scenario, stage):
     """A non-SPD block in a later chunk of tails is reported with the
     system-wide scenario index by the pipelined host entry (chunks of S = 12
     tails: [0,1) [1,3) [3,4) [4,6) [6,7) [7,9) [9,10) [10,12)); stages 2 and
-    64 are eliminated at level 0, 3 at level 1 (both run per chunk), 57 at
-    level 3 (the top kernel) and 1 is x_1."""
+    64 are eliminated at level 0 (run per chunk), 3 at level 1 (over all
+    tails), 57 at level 3 (the top kernel) and 1 is x_1."""
     bm = _bm()
     d = gen(12, 64, 4, 2, seed=5)
     pin = {k: d[k].contiguous().pin_memory() for k in ("D", "E", "C", "R", "r")}
