@@ -239,6 +239,28 @@ def test_fp64_host_entry_matches_device_entry(S, N, nb, nr, piped):
     solver.close()
 
 
+@pytest.mark.parametrize("direct", [False, True])   # captured graph, or BM_FLAG_NO_GRAPH
+def test_fp64_host_entry_pipelined_new_buffers(direct):
+    """The pipelined host entry follows new host buffers (the captured form
+    is captured again) and gives the device entry's bits for each system,
+    also when its copies and kernels are launched directly."""
+    bm = _bm()
+    flags = bm.BM_FLAG_NO_GRAPH if direct else 0
+    S, N, nb, nr = 10, 40, 6, 3
+    d1, d2 = gen(S, N, nb, nr, seed=21), gen(S, N, nb, nr, seed=22)
+    ref1, ref2 = run_gpu(d1)["x"], run_gpu(d2)["x"]
+    p1 = {k: d1[k].contiguous().pin_memory() for k in ("D", "E", "C", "R", "r")}
+    p2 = {k: d2[k].contiguous().pin_memory() for k in ("D", "E", "C", "R", "r")}
+    solver = bm.BranchKKTSolver(S, N, nb, nr, flags=flags)
+    x = torch.empty_like(p1["r"]).pin_memory()
+    for call, (p, ref) in enumerate(((p1, ref1), (p2, ref2), (p1, ref1), (p1, ref1))):
+        x, code = solver.factor_solve_host(p["D"], p["E"], p["C"], p["R"], p["r"], x)
+        assert code == 0
+        assert solver.query()["host_pipelined"] == (1 if call > 0 else 0)
+        assert np.array_equal(x.numpy(), ref)
+    solver.close()
+
+
 @pytest.mark.parametrize("scenario,stage", [(8, 2), (8, 3), (11, 57), (0, 1), (7, 64)])
 def test_fp64_host_entry_pipelined_reports_location(scenario, stage):
     """A non-SPD block in a later chunk of tails is reported with the
