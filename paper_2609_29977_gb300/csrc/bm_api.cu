@@ -512,8 +512,8 @@ static bool host_pinned(const void *p) {
 // chunk's level 0 takes about as long as its copy; running level 1 per
 // chunk as well measured slower: 8.97 against 7.93 ms per call on the mixed
 // workload, the smaller level-1 grids filling the SMs less well). The
-// remaining levels and the top kernel (whose last CTA does the root step)
-// run over all tails once every input has arrived. Every block
+// remaining levels run over all tails once the last chunk has arrived, and
+// the top kernel (whose last CTA does the root step) once C, R and r have. Every block
 // is computed by the same kernels in the same order as in bm_factor, so the
 // factor is bitwise that of the device entry. Returns false when the
 // pipelined form does not apply or could not be issued; the caller then
@@ -567,8 +567,11 @@ static bool factor_host_pipelined(bm_handle h, const double *hD, const double *h
       if (e == cudaSuccess && lp > 0)
         f64_launch_factor_part(v, (int)((long)S * c / K), (int)((long)S * (c + 1) / K), 0, lp, false, cs, sc);
     }
+    // the later levels need only the blocks; C, R and r (copied last) are
+    // first read by the top kernel
+    if (e == cudaSuccess) f64_launch_factor_part(v, 0, S, lp, 1 << 30, false, cs, sc);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, h->ev_cp[K + 1], 0);
-    if (e == cudaSuccess) f64_launch_factor_part(v, 0, S, lp, 1 << 30, true, cs, sc);
+    if (e == cudaSuccess) f64_launch_factor_part(v, 0, S, 1 << 30, 1 << 30, true, cs, sc);
     return e == cudaSuccess ? cudaPeekAtLastError() : e;
   });
   if (*out != BM_OK) {
