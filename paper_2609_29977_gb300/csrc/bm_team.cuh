@@ -230,27 +230,36 @@ __device__ __forceinline__ void team_syrk_sub(const Team<TEAM> &tm, T *sD, const
 
 // In-place lower Cholesky of sA; sInv[j] = 1/L_jj. A non-positive or
 // non-finite pivot is replaced by 1; returns 1 + its column, 0 if none.
+// Two barriers per column: the first element of each trailing update is
+// the next diagonal entry, so its lane (lane 0) takes the next pivot step
+// at once while the other lanes finish the update.
 template <int TEAM, int NB, typename T>
 __device__ __forceinline__ int team_chol(const Team<TEAM> &tm, T *sA, T *sInv) {
   int fail = 0;
-#pragma unroll 1
-  for (int j = 0; j < NB; ++j) {
-    if (tm.lane == 0) {
-      T d = sA[j * NB + j];
-      if (!pivot_ok(d)) {
-        if (!fail) fail = j + 1;
-        d = T(1);
-      }
-      const T r = rsqrt_t<T>(d);
-      sA[j * NB + j] = d * r;
-      sInv[j] = r;
+  auto pivot = [&](int j, T d) {
+    if (!pivot_ok(d)) {
+      if (!fail) fail = j + 1;
+      d = T(1);
     }
-    tm.sync();
+    const T r = rsqrt_t<T>(d);
+    sA[j * NB + j] = d * r;
+    sInv[j] = r;
+  };
+  if (tm.lane == 0) pivot(0, sA[0]);
+  tm.sync();
+#pragma unroll 1
+  for (int j = 0; j < NB - 1; ++j) {
     const T r = sInv[j];
     for (int i = j + 1 + tm.lane; i < NB; i += TEAM) sA[i * NB + j] *= r;
     tm.sync();
     const int m = NB - 1 - j, ne = m * (m + 1) / 2;
-    for (int e = tm.lane; e < ne; e += TEAM) {
+    int e0 = tm.lane;
+    if (tm.lane == 0) {   // element 0 of the trailing update is (j+1, j+1)
+      const int d = (j + 1) * NB;
+      pivot(j + 1, fma_t<T>(-sA[d + j], sA[d + j], sA[d + j + 1]));
+      e0 = TEAM;
+    }
+    for (int e = e0; e < ne; e += TEAM) {
       int a, b;
       tri_index(e, a, b);
       const int i = j + 1 + a, k = j + 1 + b;
@@ -261,17 +270,22 @@ __device__ __forceinline__ int team_chol(const Team<TEAM> &tm, T *sA, T *sInv) {
   return fail;
 }
 
-// X (M x NB) := X L^{-T}, with the inverse diagonal of L in inv.
+// X (M x NB) := X L^{-T}, with the inverse diagonal of L in inv. One
+// barrier per column: column j+1 is updated and scaled by inv[j+1] in the
+// same pass (final for step j+1), then the columns after it are updated.
 template <int TEAM, int NB, typename T>
 __device__ __forceinline__ void team_trsm_lt(const Team<TEAM> &tm, T *X, int M, const T *L, const T *inv) {
+  const T r0 = inv[0];
+  for (int row = tm.lane; row < M; row += TEAM) X[row * NB] *= r0;
+  tm.sync();
 #pragma unroll 1
-  for (int j = 0; j < NB; ++j) {
-    const T r = inv[j];
-    for (int row = tm.lane; row < M; row += TEAM) X[row * NB + j] *= r;
-    tm.sync();
-    const int cols = NB - 1 - j, ne = M * cols;
+  for (int j = 0; j < NB - 1; ++j) {
+    const T rn = inv[j + 1], l1 = L[(j + 1) * NB + j];
+    for (int row = tm.lane; row < M; row += TEAM)
+      X[row * NB + j + 1] = fma_t<T>(-X[row * NB + j], l1, X[row * NB + j + 1]) * rn;
+    const int cols = NB - 2 - j, ne = M * cols;
     for (int e = tm.lane; e < ne; e += TEAM) {
-      const int row = e / cols, k = j + 1 + (e - row * cols);
+      const int row = e / cols, k = j + 2 + (e - row * cols);
       X[row * NB + k] = fma_t<T>(-X[row * NB + j], L[k * NB + j], X[row * NB + k]);
     }
     tm.sync();
