@@ -48,3 +48,59 @@ def test_host_only_entry_points(lib):
     assert n >= 5 * 64 * 64 * 144 * 8
     assert bm.bm_workspace_bytes(bm.make_desc(0, 4, 4, 2)) == 0
     assert bm.bm_workspace_bytes(bm.make_desc(2, 4, 65, 2)) == 0
+
+
+def header_structs():
+    """(name, [field names in order]) of every `typedef struct { ... } name;`
+    in include/bm.h."""
+    src = open(os.path.join(ROOT, "include", "bm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = []
+    for body, name in re.findall(r"typedef\s+struct\s*\{(.*?)\}\s*(bm_\w+)\s*;", src, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            m = re.match(r"^((?:const\s+)?(?:unsigned\s+long\s+long|unsigned|double|int|size_t))\s+(.*)$", decl)
+            assert m, "unparsed field declaration in %s: %r" % (name, decl)
+            for d in m.group(2).split(","):
+                fields.append(re.sub(r"\[.*\]", "", d).strip().lstrip("*").strip())
+        out.append((name, fields))
+    return out
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every struct of the C ABI has a ctypes twin in the binding with the
+    same fields in the same order at the same offsets and sizes (the C side
+    measured by a C compiler on include/bm.h)."""
+    import shutil
+    import subprocess
+    from paper_2609_29977_gb300 import bm
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    structs = header_structs()
+    assert {n for n, _ in structs} >= {"bm_desc", "bm_info", "bm_qp_desc", "bm_server_desc", "bm_request",
+                                       "bm_completion", "bm_server_stats"}
+    lines = ['#include "bm.h"', "#include <stdio.h>", "#include <stddef.h>", "int main(void) {"]
+    for name, fields in structs:
+        lines.append('  printf("%s %%zu\\n", sizeof(%s));' % (name, name))
+        for f in fields:
+            lines.append('  printf("%s.%s %%zu %%zu\\n", offsetof(%s, %s), sizeof(((%s *)0)->%s));'
+                         % (name, f, name, f, name, f))
+    lines += ["  return 0;", "}"]
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I" + os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        key, *vals = line.split()
+        got[key] = tuple(int(v) for v in vals)
+    for name, fields in structs:
+        py = getattr(bm, name)
+        assert [f[0] for f in py._fields_] == fields, name
+        assert ctypes.sizeof(py) == got[name][0], name
+        for f in fields:
+            assert (getattr(py, f).offset, getattr(py, f).size) == got["%s.%s" % (name, f)], (name, f)
