@@ -251,6 +251,48 @@ def test_nb1_is_bordered_scalar_tridiagonal():
     assert np.allclose(out["x"], xref, rtol=1e-10, atol=1e-12 * np.abs(xref).max())
 
 
+def _block_thomas(D, E, rhs):
+    """Block tridiagonal solve, textbook block LU recursion: diagonal blocks
+    D[k] (full symmetric), sub-diagonal E[k] = block (k+1, k), super-diagonal
+    E[k]^T; rhs is (N*nb, m)."""
+    N, nb = D.shape[0], D.shape[1]
+    rhs = rhs.reshape(N, nb, -1)
+    Cp, dp = [None] * N, [None] * N
+    M = D[0]
+    for k in range(N):
+        if k > 0:
+            M = D[k] - E[k - 1] @ Cp[k - 1]
+        r = rhs[k] - (E[k - 1] @ dp[k - 1] if k > 0 else 0.0)
+        dp[k] = np.linalg.solve(M, r)
+        if k + 1 < N:
+            Cp[k] = np.linalg.solve(M, E[k].T)
+    x = [None] * N
+    x[-1] = dp[-1]
+    for k in range(N - 2, -1, -1):
+        x[k] = dp[k] - Cp[k] @ x[k + 1]
+    return np.concatenate(x).reshape(N * nb, -1)
+
+
+def test_s1_is_bordered_block_tridiagonal():
+    """One tail: a block tridiagonal matrix bordered by the root on its first
+    stage, solved by block Thomas recursions and the border's Schur complement."""
+    N, nb, nr = 9, 3, 2
+    d = small(1, N, nb, nr, seed=6, barrier=(-2, 2))
+    out = natural.solve_system(d)
+    D = np.array([np.tril(b) + np.tril(b, -1).T for b in d["D"][0]])
+    E = d["E"][0]
+    C, r = d["C"][0], d["r"]
+    Rl = np.tril(d["R"])
+    B = np.zeros((N * nb, nr))
+    B[:nb] = C.T                       # border: root coupled to stage 1 only
+    Z = _block_thomas(D, E, B)
+    w = _block_thomas(D, E, r[:N * nb].reshape(-1, 1))[:, 0]
+    schur = Rl + np.tril(Rl, -1).T - B.T @ Z
+    x0 = np.linalg.solve(schur, r[N * nb:] - B.T @ w)
+    xref = np.concatenate([w - Z @ x0, x0])
+    assert np.allclose(out["x"], xref, rtol=1e-10, atol=1e-12 * np.abs(xref).max())
+
+
 def test_n1_is_arrow_matrix():
     S, nb, nr = 5, 3, 2
     d = small(S, 1, nb, nr, seed=4)
